@@ -1,0 +1,72 @@
+"""Pins of the oracle's rigid-body integration and two-way coupling (Sec. 3.5; weak
+coupling as in Sec. 2.2/6): symplectic-Euler free fall in closed form, the exact per-step
+rotation angle of the normalised first-order quaternion update, and conservation of the
+total fluid + body momentum under the symmetric pressure forces of Eq.
+rigid_pressure_symmetric."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_11156_gb300 import scenes
+
+
+def _body_scene(fluid_x, center=(0.5, 0.5, 0.5), omega=(0.0, 0.0, 0.0), gravity=(0, 0, -9.81),
+                **kw):
+    pts, body = scenes.cube_body(center, 0.1, 0.02, 500.0)
+    body["omega"] = omega
+    p = scenes.params(radius=0.01, domain_min=(0, 0, 0), domain_max=(1, 1, 1),
+                      gravity=gravity, **kw)
+    d = dict(p)
+    d["fluid_x"] = np.asarray(fluid_x, np.float32).reshape(-1, 3)
+    d["fluid_v"] = np.zeros_like(d["fluid_x"])
+    d["boundary_x"] = pts
+    d["boundary_body"] = np.zeros(len(pts), np.int32)
+    d["bodies"] = [body]
+    return d
+
+
+def test_free_fall_closed_form(oracle_lib):
+    d = _body_scene([[0.05, 0.05, 0.05]], center=(0.5, 0.5, 0.8))
+    s = oracle_lib.Scene(d)
+    dt = 1e-3
+    for n in range(1, 51):
+        s.step(dt)
+        com = s.bodies()[0, 0:3]
+        vel = s.bodies()[0, 7:10]
+        assert vel[2] == pytest.approx(-9.81 * dt * n, rel=1e-12)
+        assert com[2] == pytest.approx(0.8 - 9.81 * dt * dt * n * (n + 1) / 2, rel=1e-12)
+
+
+def test_torque_free_spin_angle(oracle_lib):
+    w = np.array([0.0, 0.0, 3.0])
+    d = _body_scene([[0.05, 0.05, 0.05]], omega=tuple(w), gravity=(0, 0, 0))
+    s = oracle_lib.Scene(d)
+    dt = 1e-2
+    n = 40
+    for _ in range(n):
+        s.step(dt)
+    q = s.bodies()[0, 3:7]
+    np.testing.assert_allclose(s.bodies()[0, 10:13], w, rtol=1e-12)
+    # each step multiplies q by (1, dt w/2) and renormalises: a rotation by 2 atan(|w| dt/2)
+    angle = n * 2.0 * math.atan(3.0 * dt / 2.0)
+    np.testing.assert_allclose(q, [math.cos(angle / 2), 0, 0, math.sin(angle / 2)], atol=1e-12)
+
+
+def test_fluid_body_momentum_conserved(oracle_lib):
+    # fluid packed tightly around a free cube, no gravity, no walls: the pressure pushes
+    # both, and the total momentum of fluid plus body stays zero
+    rng = np.random.default_rng(0)
+    x = scenes.lattice_block((12, 12, 12), 0.018, (0.39, 0.39, 0.39), 2e-4, rng)
+    c = np.array([0.5, 0.5, 0.5])
+    keep = np.max(np.abs(x - c), axis=1) > 0.062
+    d = _body_scene(x[keep], center=tuple(c + [0.01, 0.0, -0.005]), gravity=(0, 0, 0),
+                    viscosity_mode=0)
+    s = oracle_lib.Scene(d)
+    M = d["bodies"][0]["mass"]
+    for _ in range(3):
+        s.step(2e-4)
+        pf = s.mass * s.get(oracle_lib.V).sum(0)
+        pb = M * s.bodies()[0, 7:10]
+        assert np.abs(pb).max() > 1e-6
+        np.testing.assert_allclose(pf + pb, 0.0, atol=1e-10 * np.abs(pb).max())
