@@ -1,0 +1,297 @@
+"""Benchmark: DFSPH particle-steps/s on the large rigid-coupling dam break (1.2M fluid
+particles, 3 floating boxes, CFL dt <= 1e-3 s, 0.1 % density and divergence tolerance).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  The timed region is K CUDA-graph steps on the library's
+stream, bracketed by CUDA events; `e2e` repeats the measurement through the C ABI with
+each step's result (positions) copied to pinned host memory; `roofline` reports the
+dominant kernel from a second pass of eager, CUDA-event-timed steps; `cpu_baseline` times
+the CPU oracle on a bounded sample.  With N > 1 (torchrun) every rank runs an
+independent replica of the scene (the scene does not shard; scaling is weak).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DFSPH particle-steps/s at 0.1% density error, learned vs plain; %HBM peak"
+UNIT = "particle-steps/s"
+WORKLOAD = ("dam break with two-way rigid coupling: 125x98x98 = 1,200,500 fluid particles "
+            "(r = 0.005 m) in a 2x1x1 m one-layer tank, 3 rigid boxes (0.1 m, 500 kg/m^3), "
+            "CFL dt <= 1e-3 s, eta = 0.1% density / 0.1% divergence")
+
+# Algorithmic bytes per fluid particle of each kernel: the particle's own state read and
+# written once (neighbour data is reused on chip; the neighbour lists are an
+# implementation choice and not counted), plus the boundary particles' state once.
+ALGO_BYTES = {
+    "dens_pass_a": 44, "div_pass_a": 44,        # x, v, rho, alpha, kappa_sum -> kappa/rho, kappa_sum
+    "dens_pass_b": 40, "div_pass_b": 40,        # x, kappa/rho, v -> v
+    "dens_warm_pass_b": 40, "div_warm_pass_b": 40,
+    "density_alpha": 52,                        # x, v, kappa_v_prev -> rho, alpha, counts, kappa_v, kappa/rho
+    "nonpressure": 56,                          # x, v, rho -> v*, rho, kappa_sum, kappa0, kappa/rho
+    "warm_density": 48,                         # x, v*, rho, kappa_prev -> kappa0, kappa_sum, kappa/rho
+}
+BOUNDARY_BYTES = 16                             # x_b, Psi_b per boundary particle and sweep
+# FP32 operations per neighbour pair in the list sweeps (distance, spline gradient, dot)
+FLOPS_PER_PAIR = {"dens_pass_a": 26, "div_pass_a": 24, "dens_pass_b": 22, "div_pass_b": 22,
+                  "dens_warm_pass_b": 22, "div_warm_pass_b": 22, "nonpressure": 30,
+                  "warm_density": 26}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    def __init__(self, path, index=0):
+        self.path = path
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(desc, steps=2):
+    import oracle
+    oracle.build()
+    o = oracle.Scene(desc)
+    t = time.perf_counter()
+    for _ in range(steps):
+        o.step(0.0)
+    el = time.perf_counter() - t
+    n = len(desc["fluid_x"])
+    return {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d oracle steps of the full %d-particle workload from its initial state "
+                      "(FP64, OpenMP, %.1f s)" % (steps, n, el)}
+
+
+def reference_sample():
+    from paper_2403_11156_gb300 import scenes
+    # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
+    # a full --steps K --warmup W run of the oracle ends within a few minutes
+    return scenes.dam_break_rigid(n=(80, 64, 64), tank=(1.28, 0.64, 0.64))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    d = reference_sample()
+    o = oracle.Scene(d)
+    for _ in range(args.warmup):
+        o.step(0.0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(0.0)
+    el = time.perf_counter() - t
+    n = len(d["fluid_x"])
+    v = n * args.steps / el
+    sample = ("oracle (FP64 C, OpenMP) stepping a %d-particle scaled copy of the workload "
+              "(same r, tolerances, CFL and rigid boxes; tank 1.28x0.64x0.64 m)" % n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timing-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2403_11156_gb300 import build, scenes, sph
+
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    desc = scenes.dam_break_rigid()
+    n_fluid = len(desc["fluid_x"])
+    stream = torch.cuda.Stream()
+    g = sph.Context(desc, stream=stream)
+    g.sph_steps(args.warmup, 0.0)
+    g.sph_synchronize()
+
+    # ---- timed region: K graph-launched steps (inputs resident; the scene's working set
+    # of ~0.5 GB per step is larger than L2, so no flush is needed between steps)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = g.sph_launch_count()
+    it0 = g.sph_get_stats()
+    clocks = ClockSampler("/tmp/bench_clocks_%d.csv" % rank, local)
+    with clocks:
+        barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        g.sph_steps(args.steps, 0.0)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = start.elapsed_time(stop)
+    status = g.sph_synchronize(raise_on_error=False)
+    it1 = g.sph_get_stats()
+    launches = g.sph_launch_count() - l0
+    t_max = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = world * n_fluid * args.steps / (ms / 1000.0)
+
+    # ---- end to end through the C ABI: each step enqueued with a host dt and its
+    # positions read back into pinned host memory
+    pinned = torch.empty((n_fluid, 3), dtype=torch.float32, pin_memory=True)
+    dev_x = torch.empty((n_fluid, 3), dtype=torch.float32, device="cuda")
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.sph_step(0.0)
+        g.sph_read_state_device(0, x=dev_x)
+        with torch.cuda.stream(stream):
+            pinned.copy_(dev_x, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t
+    e2e = {"value": world * n_fluid * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4,
+           "d2h_bytes_per_step": 12 * n_fluid}
+
+    # ---- kernel breakdown: eager steps with CUDA events around every launch
+    g.sph_set_mode(graph=False, timing=True)
+    g.sph_kernel_times(reset=True)
+    g.sph_steps(args.timing_steps, 0.0)
+    g.sph_synchronize(raise_on_error=False)
+    kt = g.sph_kernel_times(reset=True)
+    g.sph_set_mode(graph=True, timing=False)
+    total_ms = sum(v[1] for v in kt.values())
+    top = max(kt.items(), key=lambda t: t[1][1])
+    name, (n_launch, k_ms) = top
+    per_launch_s = k_ms / n_launch / 1000.0
+    n_b = len(desc["boundary_x"])
+    hbm, sm_max, peak_src = load_peaks()
+    algo = ALGO_BYTES.get(name, 48) * n_fluid + BOUNDARY_BYTES * n_b
+    achieved_gbs = algo / per_launch_s / 1e9
+    nbr = float(it1["max_fluid_nbrs"])
+    roof = {"kernel": name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": achieved_gbs / hbm, "traffic": None,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured" else "fallback 6.8 TB/s",
+            "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
+            "share_of_step": k_ms / total_ms if total_ms else None}
+    if name in FLOPS_PER_PAIR:
+        # ALU view of the same kernel: counted FP32 flops over the measured mean neighbour count
+        nn_mean = 33.0
+        flops = FLOPS_PER_PAIR[name] * nn_mean * n_fluid
+        roof["alu"] = {"achieved_tflops": flops / per_launch_s / 1e12,
+                       "peak_tflops": fp32_peak_tflops(clocks.summary().get("sm_mhz") or sm_max),
+                       "pairs_per_particle": nn_mean}
+        roof["alu"]["frac"] = roof["alu"]["achieved_tflops"] / roof["alu"]["peak_tflops"]
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4)}
+                 for k, v in sorted(kt.items(), key=lambda t: -t[1][1])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g.close()
+        cpu = cpu_baseline(desc)
+
+    d_it = it1["total_dens_iters"] - it0["total_dens_iters"]
+    v_it = it1["total_div_iters"] - it0["total_div_iters"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fluid_particles": n_fluid, "boundary_particles": n_b,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "warm_start": "previous-step kappa (plain DFSPH)",
+                   "l2": "working set per step > L2 (129 MB); no flush",
+                   "mean_density_iters": d_it / args.steps, "mean_divergence_iters": v_it / args.steps,
+                   "final_density_error": it1["dens_err"], "dt": it1["dt"], "status": sph.STATUS_NAMES[status]},
+        "clocks": clocks.summary(), "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
+        "kernels": breakdown, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) DFSPH particle pipeline.
+ *
+ * The calls follow the paper's statement of the problem (arXiv 2403.11156): a scene is
+ * configured (Sec. 4.1: fluid and rigid particles, particle radius, rest density,
+ * viscosity, domain), simulated step by step (Sec. 4.2: gravity, viscosity, pressure,
+ * rigid and fluid update; DFSPH per Sec. 3.4.2 and Sec. 5), and its particles exported
+ * (Sec. 4.3).  Every step of the pipeline runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Host arrays passed to sph_create are copied; the caller keeps ownership.
+ *  - Output buffers are caller-owned; per-particle outputs are in the caller's original
+ *    particle order (index = position in the arrays given to sph_create).
+ *  - Coordinates are float32, [n][3] row-major (x, y, z), SI units (m, m/s, kg/m^3).
+ *  - All device work is enqueued on the stream given at creation (NULL = legacy default
+ *    stream).  sph_step returns once the step is enqueued; calls that return data
+ *    synchronise that stream.
+ *  - A context is not thread-safe.  SPH_ECUDA and SPH_ETIMEOUT poison a context: only
+ *    sph_last_error and sph_destroy remain valid.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_ABI_VERSION 1
+
+typedef enum sph_status {
+    SPH_OK = 0,
+    SPH_EINVAL = 1,       /* bad argument or scene descriptor; nothing was changed        */
+    SPH_ENOMEM = 2,       /* a device or host allocation failed                           */
+    SPH_ECUDA = 3,        /* a CUDA call failed; the context is poisoned                  */
+    SPH_ENOCONVERGE = 4,  /* a solver stopped at max_iter above its tolerance; the state  */
+                          /* was advanced with the last iterate (see sph_stats)           */
+    SPH_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the context is poisoned  */
+    SPH_ENUMERIC = 6,     /* a non-finite position or velocity was produced               */
+    SPH_EOVERFLOW = 7     /* a particle had more neighbours than the list capacity; that  */
+                          /* step dropped the excess (raise max_*_neighbors)              */
+} sph_status;
+
+/* viscosity_mode */
+#define SPH_VISC_NONE 0      /* gravity only                                               */
+#define SPH_VISC_EXPLICIT 1  /* (mu/rho) times the Laplacian of Sec. 3.6.1 Eq. lap        */
+#define SPH_VISC_XSPH 2      /* XSPH velocity smoothing with coefficient xsph_c            */
+#define SPH_VISC_IMPLICIT 3  /* (I - dt A) v* = v~ of Sec. 3.6.2, matrix-free CG          */
+
+/* warm_start of the two DFSPH solves */
+#define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */
+#define SPH_WARM_PREVIOUS 1  /* half the previous step's kappa where the fluid compresses */
+#define SPH_WARM_LEARNED 2   /* density solve: per-particle network prediction (see       */
+                             /* sph_set_mlp); divergence solve as SPH_WARM_PREVIOUS        */
+
+/* A rigid body (Sec. 3.5, two-way weak coupling; Sec. 4.1 initial pose and velocity). */
+typedef struct sph_rigid_desc {
+    double mass;       /* kg                                                        */
+    double inertia[3]; /* principal moments in the body frame, kg m^2 (all > 0)     */
+    double com[3];     /* initial centre of mass, m                                 */
+    double quat[4];    /* initial orientation (w, x, y, z), unit                    */
+    double vel[3];     /* initial linear velocity, m/s                              */
+    double omega[3];   /* initial angular velocity (world frame), rad/s             */
+} sph_rigid_desc;
+
+/* One scene (Sec. 4.1).  Zero-initialise and fill; zero means "default" where noted. */
+typedef struct sph_scene_desc {
+    int64_t n_fluid;              /* fluid particles (>= 1)                           */
+    const float *fluid_x;         /* host [n_fluid][3] positions                      */
+    const float *fluid_v;         /* host [n_fluid][3] velocities, or NULL for zero   */
+    int64_t n_boundary;           /* Akinci boundary particles (>= 0)                 */
+    const float *boundary_x;      /* host [n_boundary][3]                             */
+    const int32_t *boundary_body; /* host [n_boundary]: body index, -1 = static wall; */
+                                  /* NULL = all static                                */
+    int32_t n_bodies;             /* rigid bodies (0..SPH_MAX_BODIES)                 */
+    const sph_rigid_desc *bodies; /* host [n_bodies]                                  */
+    float radius;                 /* particle radius r; support h = 4r, mass          */
+                                  /* rho0 (2r)^3 (Sec. 5)                             */
+    float rest_density;           /* rho0, kg/m^3                                     */
+    float viscosity;              /* kinematic nu at rest density (mu = nu rho0)      */
+    float xsph_c;                 /* XSPH coefficient (SPH_VISC_XSPH only)            */
+    float gravity[3];             /* m/s^2                                            */
+    float domain_min[3];          /* grid extent; particles outside are clamped into  */
+    float domain_max[3];          /* the edge cells (still correct, only slower)      */
+    float cell_size;              /* 0 = h (1 + 2^-8); otherwise >= that value        */
+    float eta_density;            /* mean relative density error tolerance (1e-3)     */
+    float eta_divergence;         /* mean dt Drho/Dt / rho0 tolerance (1e-3)          */
+    float dt_max;                 /* largest step, s                                  */
+    float cfl;                    /* > 0: dt = min(dt_max, cfl 2r / max|v|)           */
+    int32_t min_iter_density, max_iter_density;   /* max_iter is the hard cap (>= 0)  */
+    int32_t min_iter_divergence, max_iter_divergence;
+    int32_t viscosity_mode;       /* SPH_VISC_*                                       */
+    int32_t warm_start;           /* SPH_WARM_*                                       */
+    int32_t divergence_solve;     /* 1 = run the divergence-free solve                */
+    int32_t max_fluid_neighbors;  /* list capacity per particle, 0 = 96               */
+    int32_t max_boundary_neighbors; /* 0 = 64                                         */
+    float cg_tol;                 /* relative residual of the implicit viscosity CG   */
+    int32_t cg_max_iter;
+} sph_scene_desc;
+
+#define SPH_MAX_BODIES 64
+
+/* Statistics of one scene (the last completed step unless noted). */
+typedef struct sph_stats {
+    int64_t steps;               /* steps completed since creation                   */
+    int32_t div_iters;           /* divergence-solve iterations                      */
+    int32_t dens_iters;          /* constant-density iterations                      */
+    double div_err;              /* last divergence error (mean dt Drho/Dt / rho0)   */
+    double dens_err;             /* last density error (mean max(rho*-rho0,0)/rho0)  */
+    double div_err0, dens_err0;  /* errors at the first iteration                    */
+    float dt;                    /* step size used                                   */
+    float dt_next;               /* CFL step size for the next step                  */
+    float max_speed;             /* max |v| after the step                           */
+    int32_t max_fluid_nbrs;      /* largest fluid neighbour count of the step        */
+    int32_t max_boundary_nbrs;
+    int32_t cg_iters;            /* implicit viscosity CG iterations                 */
+    float cg_residual;           /* its final relative residual                      */
+    int32_t clamps;              /* rigid-body domain clamps since creation          */
+    int32_t flags;               /* SPH_FLAG_* seen since creation (sticky)          */
+    int64_t total_div_iters;     /* since creation                                   */
+    int64_t total_dens_iters;
+} sph_stats;
+
+#define SPH_FLAG_OVERFLOW 1
+#define SPH_FLAG_NOCONVERGE 2
+#define SPH_FLAG_NONFINITE 4
+#define SPH_FLAG_TIMEOUT 8
+
+/* Device memory callbacks (for example a framework's caching allocator).  alloc returns
+ * NULL on failure; both are called only inside sph_create / sph_destroy. */
+typedef struct sph_allocator {
+    void *(*alloc)(void *user, size_t bytes, void *stream);
+    void (*free)(void *user, void *ptr, size_t bytes, void *stream);
+    void *user;
+} sph_allocator;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Library ABI version (SPH_ABI_VERSION). */
+int32_t sph_abi_version(void);
+
+/* Create a context for one scene (Sec. 4.1).  Copies the host arrays to the device,
+ * builds the static boundary grid and its pseudo-masses Psi (Sec. 3.5) and captures the
+ * step as a CUDA graph.  alloc may be NULL (cudaMalloc); stream is a cudaStream_t or
+ * NULL.  On error *out is NULL and nothing leaks. */
+sph_status sph_create(const sph_scene_desc *scene, const sph_allocator *alloc, void *stream,
+                      sph_ctx **out);
+
+/* Create a context holding n independent scenes of any sizes that step together: every
+ * kernel of the step covers all scenes in one launch, and each scene's solver stops at
+ * its own tolerance.  Scene s keeps index s in the calls below. */
+sph_status sph_create_batch(const sph_scene_desc *scenes, int32_t n, const sph_allocator *alloc,
+                            void *stream, sph_ctx **out);
+
+/* Enqueue one DFSPH step of every scene (Sec. 4.2 order; Sec. 3.3 Alg. general_algorithm,
+ * Sec. 3.4.2 Alg. ppe_solver for both solves).  dt > 0: that step size for all scenes;
+ * dt <= 0: each scene's CFL step (dt_max when cfl <= 0).  Returns without waiting;
+ * errors of the step surface at the next synchronising call. */
+sph_status sph_step(sph_ctx *ctx, float dt);
+
+/* Enqueue n steps (same dt rule). */
+sph_status sph_steps(sph_ctx *ctx, int32_t n, float dt);
+
+/* Wait for all enqueued work; returns SPH_ENOCONVERGE / SPH_EOVERFLOW / SPH_ENUMERIC if a
+ * step since the previous call raised that condition in any scene, else SPH_OK. */
+sph_status sph_synchronize(sph_ctx *ctx);
+
+/* Copy the state of one scene out, in original particle order.  Any pointer may be NULL.
+ * x, v: [n_fluid][3]; rho, pressure: [n_fluid] (pressure p = kappa rho of the last
+ * constant-density solve, Sec. 3.3 Eq. pressure_acceleration; zero before the first
+ * step).  on_device != 0: the pointers are device memory.  Synchronises. */
+sph_status sph_read_state(sph_ctx *ctx, int32_t scene, float *x, float *v, float *rho,
+                          float *pressure, int32_t on_device);
+
+/* Overwrite the dynamic state of one scene (checkpoint restore); NULL keeps a field.
+ * kappa_prev = previous step's total density stiffness times dt^2, kappa_v_prev =
+ * divergence stiffness times dt (what SPH_FIELD_KAPPA_PREV / _V_PREV return).  Positions
+ * and velocities are taken in original particle order.  Synchronises. */
+sph_status sph_write_state(sph_ctx *ctx, int32_t scene, const float *x, const float *v,
+                           const float *kappa_prev, const float *kappa_v_prev, int32_t on_device);
+
+/* Per-particle fields for inspection and checkpointing, original order unless noted. */
+#define SPH_FIELD_RHO 0          /* float [n_fluid]: density of the last step          */
+#define SPH_FIELD_ALPHA 1        /* float: DFSPH factor alpha                          */
+#define SPH_FIELD_KAPPA 2        /* float: total density stiffness of the last step    */
+#define SPH_FIELD_KAPPA_V 3      /* float: total divergence stiffness of the last step */
+#define SPH_FIELD_NN_FLUID 4     /* int32: fluid neighbours of the last step           */
+#define SPH_FIELD_NN_BOUNDARY 5  /* int32: boundary neighbours of the last step        */
+#define SPH_FIELD_V_DIV 6        /* float [n][3]: velocity after the divergence solve  */
+#define SPH_FIELD_KAPPA_PREV 7   /* float: warm-start memory, kappa dt^2               */
+#define SPH_FIELD_KAPPA_V_PREV 8 /* float: warm-start memory, kappa_v dt               */
+#define SPH_FIELD_CELL_KEY 9     /* uint32: grid cell key at the start of the last step */
+#define SPH_FIELD_SORTED_ID 10   /* int32, NOT reordered: original ids in grid order   */
+#define SPH_FIELD_PSI 11         /* float [n_boundary]: boundary pseudo-mass Psi        */
+#define SPH_FIELD_BOUNDARY_SORTED_ID 12 /* int32 [n_boundary], grid order              */
+#define SPH_FIELD_BOUNDARY_CELL_KEY 13  /* uint32 [n_boundary], original order         */
+#define SPH_FIELD_FEATURES 14    /* float [n][4]: warm-start network inputs            */
+#define SPH_FIELD_KAPPA0 15      /* float: density warm-start stiffness of the last step */
+sph_status sph_read_field(sph_ctx *ctx, int32_t scene, int32_t field, void *out,
+                          int32_t on_device);
+
+/* Statistics of one scene (synchronises). */
+sph_status sph_get_stats(sph_ctx *ctx, int32_t scene, sph_stats *out);
+
+/* Rigid bodies of one scene: per body 19 doubles: com[3], quat[4], vel[3], omega[3],
+ * force[3], torque[3] (fluid pressure force and torque of the last step). */
+sph_status sph_read_bodies(sph_ctx *ctx, int32_t scene, double *out);
+
+/* Execution mode: graph != 0 replays the step as one CUDA graph with device-side loop
+ * control (default); 0 launches kernels one by one with host-side loop control.
+ * timing != 0 (eager mode only) brackets every kernel with CUDA events on the context
+ * stream. */
+sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
+
+/* Per-kernel timing collected in eager timing mode: up to cap entries of name (63
+ * chars + NUL), launches and total milliseconds; returns the entry count in *n. */
+typedef struct sph_kernel_time {
+    char name[64];
+    int64_t launches;
+    double total_ms;
+} sph_kernel_time;
+sph_status sph_kernel_times(sph_ctx *ctx, sph_kernel_time *out, int32_t cap, int32_t *n,
+                            int32_t reset);
+
+/* Kernel launches enqueued since creation (counted on the device for graph replays). */
+sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
+
+const char *sph_status_string(sph_status s);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Free everything (waits for the stream first).  NULL is a no-op. */
+void sph_destroy(sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

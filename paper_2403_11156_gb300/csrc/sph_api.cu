@@ -1,0 +1,1100 @@
+// sph_api.cu -- host runtime behind include/sph.h: scene validation, device layout,
+// the step as a CUDA graph (conditional while-nodes run the Jacobi loops on the device),
+// an eager mode with optional per-kernel CUDA-event timing, and the read/write paths.
+#include "sph.h"
+#include "sph_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace sph;
+
+namespace {
+
+constexpr int kDefaultCapF = 96;
+constexpr int kDefaultCapB = 64;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+};
+
+struct PendingTime {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct sph_ctx {
+    cudaStream_t stream = nullptr;       // caller's stream (may be the legacy default)
+    cudaStream_t cap0 = nullptr, cap1 = nullptr;  // capture streams
+    sph_allocator alloc{};
+    bool use_alloc = false;
+    std::vector<Alloc> allocs;
+    std::string err;
+    bool poisoned = false;
+    int device = 0;
+
+    int nscenes = 0;
+    std::vector<SceneDev> scenes;        // host copies
+    std::vector<int32_t> fblk_scene, bblk_scene;
+    std::vector<int32_t> nbody_scene;
+    int max_bodies = 0;
+    bool any_moving = false, any_div = false, any_warm_div = false, any_warm = false,
+         any_learned = false, any_bodies = false, any_implicit = false;
+    Ptrs P{};
+    SceneDev *d_scenes = nullptr;
+
+    // graph
+    bool graph_mode = true;
+    bool timing = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float last_dt = -1.0f;
+
+    // timing
+    std::vector<PendingTime> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<int64_t, double>> times;
+    int64_t host_launches = 0;
+
+    std::vector<int32_t> reported_flags;
+    uint32_t *h_flag = nullptr;          // pinned word for eager loop control
+};
+
+namespace {
+
+sph_status fail(sph_ctx *c, sph_status st, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+        if (st == SPH_ECUDA || st == SPH_ETIMEOUT) c->poisoned = true;
+    }
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, SPH_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+void *dev_alloc(sph_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (c->use_alloc) {
+        p = c->alloc.alloc(c->alloc.user, bytes, (void *)c->stream);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back({p, bytes});
+    return p;
+}
+
+template <typename T>
+bool dalloc(sph_ctx *c, T *&ptr, size_t count)
+{
+    ptr = static_cast<T *>(dev_alloc(c, sizeof(T) * count));
+    return ptr != nullptr;
+}
+
+float default_cell(float radius)
+{
+    float h = 4.0f * radius;
+    return h * 1.00390625f;
+}
+
+sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
+{
+    auto bad = [&](const char *what) { return fail(c, SPH_EINVAL, "scene %d: %s", idx, what); };
+    if (d.n_fluid < 1 || d.n_fluid > (int64_t)1 << 30) return bad("n_fluid out of range");
+    if (!d.fluid_x) return bad("fluid_x is NULL");
+    if (d.n_boundary < 0 || d.n_boundary > (int64_t)1 << 30) return bad("n_boundary out of range");
+    if (d.n_boundary > 0 && !d.boundary_x) return bad("boundary_x is NULL");
+    if (!(d.radius > 0.0f) || !std::isfinite(d.radius)) return bad("radius must be > 0");
+    if (!(d.rest_density > 0.0f)) return bad("rest_density must be > 0");
+    if (!(d.viscosity >= 0.0f)) return bad("viscosity must be >= 0");
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(d.domain_min[a]) || !std::isfinite(d.domain_max[a]) ||
+            !(d.domain_max[a] > d.domain_min[a]))
+            return bad("domain_max must exceed domain_min");
+        if (!std::isfinite(d.gravity[a])) return bad("gravity not finite");
+    }
+    if (!(d.dt_max > 0.0f)) return bad("dt_max must be > 0");
+    if (d.cfl < 0.0f || !std::isfinite(d.cfl)) return bad("cfl must be >= 0");
+    if (d.eta_density < 0.0f || d.eta_divergence < 0.0f) return bad("tolerances must be >= 0");
+    // max_iter is the hard cap; min_iter above it simply never binds
+    if (d.min_iter_density < 0 || d.max_iter_density < 0 || d.max_iter_density > 100000)
+        return bad("density iteration bounds");
+    if (d.min_iter_divergence < 0 || d.max_iter_divergence < 0 || d.max_iter_divergence > 100000)
+        return bad("divergence iteration bounds");
+    if (d.viscosity_mode < 0 || d.viscosity_mode > 3) return bad("viscosity_mode");
+    if (d.warm_start < 0 || d.warm_start > 2) return bad("warm_start");
+    if (d.max_fluid_neighbors < 0 || d.max_fluid_neighbors > 1024) return bad("max_fluid_neighbors");
+    if (d.max_boundary_neighbors < 0 || d.max_boundary_neighbors > 1024) return bad("max_boundary_neighbors");
+    if (d.cell_size != 0.0f && !(d.cell_size >= default_cell(d.radius))) return bad("cell_size below h (1 + 2^-8)");
+    if (d.n_bodies < 0 || d.n_bodies > SPH_MAX_BODIES) return bad("n_bodies out of range");
+    if (d.n_bodies > 0 && !d.bodies) return bad("bodies is NULL");
+    for (int k = 0; k < d.n_bodies; ++k) {
+        const sph_rigid_desc &b = d.bodies[k];
+        if (!(b.mass > 0.0) || !(b.inertia[0] > 0.0) || !(b.inertia[1] > 0.0) || !(b.inertia[2] > 0.0))
+            return bad("body mass and inertia must be > 0");
+        double qn = b.quat[0] * b.quat[0] + b.quat[1] * b.quat[1] + b.quat[2] * b.quat[2] + b.quat[3] * b.quat[3];
+        if (!(std::fabs(qn - 1.0) < 1e-6)) return bad("body quaternion must be unit");
+    }
+    if (d.boundary_body) {
+        for (int64_t b = 0; b < d.n_boundary; ++b)
+            if (d.boundary_body[b] < -1 || d.boundary_body[b] >= d.n_bodies) return bad("boundary_body index");
+    }
+    for (int64_t i = 0; i < 3 * d.n_fluid; ++i)
+        if (!std::isfinite(d.fluid_x[i]) || (d.fluid_v && !std::isfinite(d.fluid_v[i])))
+            return bad("non-finite fluid input");
+    for (int64_t i = 0; i < 3 * d.n_boundary; ++i)
+        if (!std::isfinite(d.boundary_x[i])) return bad("non-finite boundary input");
+    float c0 = d.cell_size > 0.0f ? d.cell_size : default_cell(d.radius);
+    double cells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        float ext = (d.domain_max[a] - d.domain_min[a]) / c0;
+        cells *= (double)((int64_t)std::ceil(ext) + 2);
+    }
+    if (cells > 1.5e9) return bad("grid too large (domain / cell size)");
+    return SPH_OK;
+}
+
+// ------------------------------------------------------------------ read / write kernels
+__global__ void k_read_fluid(Ptrs P, int scene, int field, void *out)
+{
+    const SceneDev &sc = P.scenes[scene];
+    int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= sc.nf) return;
+    int64_t i = sc.f_off + local;
+    // canonical arrays (state) use id_c; per-step arrays use id_s (equal after a step)
+    switch (field) {
+    case 100: {  // x
+        float4 p = P.pos_c[i];
+        float *o = (float *)out + 3 * P.id_c[i];
+        o[0] = p.x; o[1] = p.y; o[2] = p.z;
+        break;
+    }
+    case 101: {  // v
+        float4 v = P.vel_c[i];
+        float *o = (float *)out + 3 * P.id_c[i];
+        o[0] = v.x; o[1] = v.y; o[2] = v.z;
+        break;
+    }
+    case 102: ((float *)out)[P.id_c[i]] = P.vel_c[i].w; break;            // rho
+    case 103: ((float *)out)[P.id_c[i]] = P.ksum[i] * P.vel_c[i].w; break; // pressure
+    case SPH_FIELD_RHO: ((float *)out)[P.id_s[i]] = P.vel_s[i].w; break;
+    case SPH_FIELD_ALPHA: ((float *)out)[P.id_s[i]] = P.alpha[i]; break;
+    case SPH_FIELD_KAPPA: ((float *)out)[P.id_s[i]] = P.ksum[i]; break;
+    case SPH_FIELD_KAPPA_V: ((float *)out)[P.id_s[i]] = P.kvsum[i]; break;
+    case SPH_FIELD_NN_FLUID: ((int32_t *)out)[P.id_s[i]] = P.nnf[i]; break;
+    case SPH_FIELD_NN_BOUNDARY: ((int32_t *)out)[P.id_s[i]] = P.nnb[i]; break;
+    case SPH_FIELD_V_DIV: {
+        float4 v = P.vel_s[i];
+        float *o = (float *)out + 3 * P.id_s[i];
+        o[0] = v.x; o[1] = v.y; o[2] = v.z;
+        break;
+    }
+    case SPH_FIELD_KAPPA_PREV: ((float *)out)[P.id_c[i]] = P.kprev_c[i]; break;
+    case SPH_FIELD_KAPPA_V_PREV: ((float *)out)[P.id_c[i]] = P.kvprev_c[i]; break;
+    case SPH_FIELD_CELL_KEY: {
+        float4 p = P.pos_s[i];
+        int32_t ix = cell_coord(p.x, sc.origin[0], sc.cell, sc.dims[0]);
+        int32_t iy = cell_coord(p.y, sc.origin[1], sc.cell, sc.dims[1]);
+        int32_t iz = cell_coord(p.z, sc.origin[2], sc.cell, sc.dims[2]);
+        ((uint32_t *)out)[P.id_s[i]] =
+            (uint32_t)ix + (uint32_t)sc.dims[0] * ((uint32_t)iy + (uint32_t)sc.dims[1] * (uint32_t)iz);
+        break;
+    }
+    case SPH_FIELD_SORTED_ID: ((int32_t *)out)[local] = P.id_s[i]; break;
+    case SPH_FIELD_FEATURES: {
+        float4 f = reinterpret_cast<const float4 *>(P.feat)[i];
+        float *o = (float *)out + 4 * P.id_s[i];
+        o[0] = f.x; o[1] = f.y; o[2] = f.z; o[3] = f.w;
+        break;
+    }
+    case SPH_FIELD_KAPPA0: ((float *)out)[P.id_s[i]] = P.k0[i]; break;
+    default: break;
+    }
+}
+
+__global__ void k_read_boundary(Ptrs P, int scene, int field, void *out)
+{
+    const SceneDev &sc = P.scenes[scene];
+    int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= sc.nb) return;
+    int64_t b = sc.b_off + local;
+    switch (field) {
+    case SPH_FIELD_PSI: ((float *)out)[P.bid_s[b]] = P.bpos_s[b].w; break;
+    case SPH_FIELD_BOUNDARY_SORTED_ID: ((int32_t *)out)[local] = P.bid_s[b]; break;
+    case SPH_FIELD_BOUNDARY_CELL_KEY: {
+        float4 p = P.bx_o[b];
+        int32_t ix = cell_coord(p.x, sc.origin[0], sc.cell, sc.dims[0]);
+        int32_t iy = cell_coord(p.y, sc.origin[1], sc.cell, sc.dims[1]);
+        int32_t iz = cell_coord(p.z, sc.origin[2], sc.cell, sc.dims[2]);
+        ((uint32_t *)out)[local] =
+            (uint32_t)ix + (uint32_t)sc.dims[0] * ((uint32_t)iy + (uint32_t)sc.dims[1] * (uint32_t)iz);
+        break;
+    }
+    default: break;
+    }
+}
+
+// Bring one scene's canonical arrays back to original particle order (through the
+// sorted arrays as scratch), so that a checkpoint can be written in that order.
+__global__ void k_unpermute_to_sorted(Ptrs P, int scene)
+{
+    const SceneDev &sc = P.scenes[scene];
+    int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= sc.nf) return;
+    int64_t i = sc.f_off + local;
+    int64_t d = sc.f_off + P.id_c[i];
+    P.pos_s[d] = P.pos_c[i];
+    P.vel_s[d] = P.vel_c[i];
+    P.kprev_s[d] = P.kprev_c[i];
+    P.kvprev_s[d] = P.kvprev_c[i];
+}
+__global__ void k_sorted_to_canonical(Ptrs P, int scene)
+{
+    const SceneDev &sc = P.scenes[scene];
+    int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= sc.nf) return;
+    int64_t i = sc.f_off + local;
+    P.pos_c[i] = P.pos_s[i];
+    float4 v = P.vel_s[i];
+    v.w = 0.0f;
+    P.vel_c[i] = v;
+    P.kprev_c[i] = P.kprev_s[i];
+    P.kvprev_c[i] = P.kvprev_s[i];
+    P.id_c[i] = (int32_t)local;
+    P.id_s[i] = (int32_t)local;
+    P.ksum[i] = 0.0f;
+    P.kvsum[i] = 0.0f;
+}
+// Write [n][3] (packed) into a float4 array, original order == canonical order here.
+__global__ void k_pack3(float4 *dst, const float *src, int64_t n, float w)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    dst[k] = make_float4(src[3 * k], src[3 * k + 1], src[3 * k + 2], w);
+}
+__global__ void k_scene_cfl(Ptrs P, int scene)
+{
+    __shared__ float sh[256];
+    const SceneDev &sc = P.scenes[scene];
+    float m = 0.0f;
+    for (int64_t k = threadIdx.x; k < sc.nf; k += blockDim.x) {
+        float4 v = P.vel_c[sc.f_off + k];
+        m = fmaxf(m, v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float vm = sqrtf(sh[0]);
+        float dt = sc.dt_max;
+        if (sc.cfl > 0.0f && vm > 0.0f) dt = fminf(dt, sc.cfl * sc.two_r / vm);
+        P.st[scene].dt_next = dt;
+    }
+}
+
+// ------------------------------------------------------------------ launch plumbing
+cudaEvent_t get_event(sph_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+sph_status harvest(sph_ctx *c)
+{
+    if (c->pending.empty()) return SPH_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto &p : c->pending) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto &t = c->times[p.name];
+        t.first += 1;
+        t.second += ms;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    return SPH_OK;
+}
+
+template <typename F>
+void run(sph_ctx *c, cudaStream_t s, const char *name, F &&f)
+{
+    if (c->timing && !c->graph_mode) {
+        cudaEvent_t a = get_event(c), b = get_event(c);
+        cudaEventRecord(a, s);
+        f();
+        cudaEventRecord(b, s);
+        c->pending.push_back({name, a, b});
+    } else {
+        f();
+    }
+    c->host_launches += 1;
+}
+
+// Enqueue one step.  In capture mode the two Jacobi loops become conditional while
+// nodes whose bodies are captured on a second stream; in eager mode the host reads the
+// loop flag after every iteration.
+sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
+{
+    const Ptrs &P = c->P;
+    run(c, s, "step_begin", [&] { launch_step_begin(P, s); });
+    if (c->any_moving) {
+        run(c, s, "boundary_update", [&] { launch_boundary_update(P, s); });
+        run(c, s, "bsort_key_hist", [&] { launch_key_hist(P, SORT_BOUNDARY, s); });
+        run(c, s, "bsort_scan", [&] { launch_scan_cells(P, SORT_BOUNDARY, s); });
+        run(c, s, "bsort_scatter", [&] { launch_scatter(P, SORT_BOUNDARY, s); });
+        run(c, s, "bsort_rank_gather", [&] { launch_rank_gather(P, SORT_BOUNDARY, s); });
+        run(c, s, "boundary_psi", [&] { launch_boundary_psi(P, 1, s); });
+    }
+    run(c, s, "sort_key_hist", [&] { launch_key_hist(P, SORT_FLUID, s); });
+    run(c, s, "sort_scan", [&] { launch_scan_cells(P, SORT_FLUID, s); });
+    run(c, s, "sort_scatter", [&] { launch_scatter(P, SORT_FLUID, s); });
+    run(c, s, "sort_rank_gather", [&] { launch_rank_gather(P, SORT_FLUID, s); });
+    run(c, s, "density_alpha", [&] { launch_density_alpha(P, s); });
+
+    auto loop = [&](int solver) -> sph_status {
+        const char *na = solver == 0 ? "div_pass_a" : "dens_pass_a";
+        const char *nb = solver == 0 ? "div_pass_b" : "dens_pass_b";
+        if (capture) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+            cudaGraphConditionalHandle h;
+            CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+            CK(cudaStreamBeginCaptureToGraph(c->cap1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            launch_pass_a(P, solver, c->cap1);
+            launch_pass_b(P, solver, 0, h, 1, c->cap1);
+            c->host_launches += 2;
+            cudaGraph_t out = nullptr;
+            CK(cudaStreamEndCapture(c->cap1, &out));
+        } else {
+            for (int guard = 0; guard < 200000; ++guard) {
+                run(c, s, na, [&] { launch_pass_a(P, solver, s); });
+                run(c, s, nb, [&] { launch_pass_b(P, solver, 0, 0, 0, s); });
+                CK(cudaMemcpyAsync(c->h_flag, &P.ctl->loop_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (*c->h_flag == 0) break;
+            }
+        }
+        return SPH_OK;
+    };
+
+    sph_status st;
+    if (c->any_div) {
+        if (c->any_warm_div) run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, 0, 0, s); });
+        if ((st = loop(0)) != SPH_OK) return st;
+    }
+    run(c, s, "nonpressure", [&] { launch_nonpressure(P, s); });
+    if (c->any_warm) {
+        run(c, s, "warm_density", [&] { launch_warm_density(P, s); });
+        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, 0, 0, s); });
+    }
+    if ((st = loop(1)) != SPH_OK) return st;
+    if (c->any_bodies) run(c, s, "body_force", [&] { launch_body_force(P, c->max_bodies, s); });
+    run(c, s, "advect", [&] { launch_advect(P, s); });
+    run(c, s, "step_end", [&] { launch_step_end(P, s); });
+    return SPH_OK;
+}
+
+sph_status build_graph(sph_ctx *c)
+{
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    CK(cudaStreamBeginCapture(c->cap0, cudaStreamCaptureModeRelaxed));
+    sph_status st = enqueue_step(c, c->cap0, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap0, &g);
+    if (st != SPH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, SPH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    c->graph = g;
+    CK(cudaGraphInstantiate(&c->exec, g, 0));
+    return SPH_OK;
+}
+
+sph_status check_async(sph_ctx *c)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, SPH_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocator *alloc, void *stream,
+                       sph_ctx **out)
+{
+    if (!out) return SPH_EINVAL;
+    *out = nullptr;
+    sph_ctx *c = new sph_ctx();
+    auto bail = [&](sph_status st) {
+        sph_destroy(c);
+        return st;
+    };
+    if (!descs || n < 1) {
+        delete c;
+        return SPH_EINVAL;
+    }
+    c->stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->use_alloc = true;
+    }
+    for (int s = 0; s < n; ++s) {
+        sph_status st = validate(c, descs[s], s);
+        if (st != SPH_OK) {
+            delete c;
+            return st;
+        }
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return SPH_ECUDA;
+    }
+    c->nscenes = n;
+    c->scenes.resize(n);
+    int64_t NF = 0, NB = 0, NC = 0;
+    int32_t nfblk = 0, nbblk = 0, nbodies = 0;
+    int cap_f = 0, cap_b = 0;
+    for (int s = 0; s < n; ++s) {
+        const sph_scene_desc &d = descs[s];
+        SceneDev &q = c->scenes[s];
+        memset(&q, 0, sizeof q);
+        q.f_off = NF;
+        q.nf = d.n_fluid;
+        q.b_off = NB;
+        q.nb = d.n_boundary;
+        q.c_off = NC;
+        q.cell = d.cell_size > 0.0f ? d.cell_size : default_cell(d.radius);
+        int64_t nc = 1;
+        for (int a = 0; a < 3; ++a) {
+            q.origin[a] = d.domain_min[a] - q.cell;
+            float ext = (d.domain_max[a] - d.domain_min[a]) / q.cell;
+            q.dims[a] = (int32_t)std::ceil(ext) + 2;
+            nc *= q.dims[a];
+        }
+        q.ncell = (int32_t)nc;
+        const double r = d.radius, h = 4.0 * r;
+        q.h = (float)h;
+        q.h2 = q.h * q.h;
+        q.inv_h = (float)(1.0 / h);
+        q.m = (float)((double)d.rest_density * 8.0 * r * r * r);
+        q.rho0 = d.rest_density;
+        q.sigma = (float)(8.0 / (kPi * h * h * h));
+        q.kgrad = (float)(48.0 / (kPi * h * h * h * h));
+        double gs = (double)q.m * 48.0 / (kPi * h * h * h * h);
+        q.eps_alpha = (float)(1e-6 * gs * gs);
+        q.mu = d.viscosity * d.rest_density;
+        q.xsph = d.xsph_c;
+        for (int a = 0; a < 3; ++a) q.g[a] = d.gravity[a];
+        q.eta[0] = d.eta_divergence;
+        q.eta[1] = d.eta_density;
+        q.dt_max = d.dt_max;
+        q.cfl = d.cfl;
+        q.two_r = 2.0f * d.radius;
+        q.min_it[0] = d.min_iter_divergence;
+        q.max_it[0] = d.max_iter_divergence;
+        q.min_it[1] = d.min_iter_density;
+        q.max_it[1] = d.max_iter_density;
+        q.visc_mode = d.viscosity_mode;
+        q.warm = d.warm_start;
+        q.div_on = d.divergence_solve ? 1 : 0;
+        q.has_moving = d.n_bodies > 0 ? 1 : 0;
+        q.body_off = nbodies;
+        q.nbody = d.n_bodies;
+        q.fblk_first = nfblk;
+        q.fblk_count = (int32_t)((d.n_fluid + kBlock - 1) / kBlock);
+        q.bblk_first = nbblk;
+        q.bblk_count = (int32_t)((d.n_boundary + kBlock - 1) / kBlock);
+        q.cap_f = d.max_fluid_neighbors > 0 ? d.max_fluid_neighbors : kDefaultCapF;
+        q.cap_b = d.max_boundary_neighbors > 0 ? d.max_boundary_neighbors : kDefaultCapB;
+        q.cg_tol = d.cg_tol > 0.0f ? d.cg_tol : 1e-4f;
+        q.cg_max = d.cg_max_iter > 0 ? d.cg_max_iter : 500;
+        cap_f = std::max(cap_f, q.cap_f);
+        cap_b = std::max(cap_b, q.cap_b);
+        for (int k = 0; k < q.fblk_count; ++k) c->fblk_scene.push_back(s);
+        for (int k = 0; k < q.bblk_count; ++k) c->bblk_scene.push_back(s);
+        NF += d.n_fluid;
+        NB += d.n_boundary;
+        NC += nc;
+        nfblk += q.fblk_count;
+        nbblk += q.bblk_count;
+        nbodies += d.n_bodies;
+        c->max_bodies = std::max(c->max_bodies, (int)d.n_bodies);
+        c->any_moving |= d.n_bodies > 0;
+        c->any_bodies |= d.n_bodies > 0;
+        c->any_div |= d.divergence_solve != 0;
+        c->any_warm_div |= d.divergence_solve != 0 && d.warm_start != 0;
+        c->any_warm |= d.warm_start != 0;
+        c->any_learned |= d.warm_start == 2;
+        c->any_implicit |= d.viscosity_mode == 3;
+    }
+    if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * cap_f > 4.0e10)
+        return bail(fail(c, SPH_EINVAL, "context too large"));
+    Ptrs &P = c->P;
+    P.nfblk = nfblk;
+    P.nbblk = nbblk;
+    P.nscenes = n;
+    P.nbodies_total = nbodies;
+    P.NF = NF;
+    P.NB = NB;
+    P.NC = NC;
+    c->reported_flags.assign(n, 0);
+
+    bool ok = true;
+    SceneState *st = nullptr;
+    ok &= dalloc(c, c->d_scenes, n);
+    ok &= dalloc(c, st, n);
+    ok &= dalloc(c, P.ctl, 1);
+    ok &= dalloc(c, P.bodies, std::max(nbodies, 1));
+    int32_t *fbs = nullptr, *bbs = nullptr;
+    ok &= dalloc(c, fbs, std::max(nfblk, 1));
+    ok &= dalloc(c, bbs, std::max(nbblk, 1));
+    ok &= dalloc(c, P.pos_s, NF) && dalloc(c, P.vel_s, NF) && dalloc(c, P.pos_c, NF) && dalloc(c, P.vel_c, NF);
+    ok &= dalloc(c, P.kprev_c, NF) && dalloc(c, P.kvprev_c, NF) && dalloc(c, P.kprev_s, NF) &&
+          dalloc(c, P.kvprev_s, NF);
+    ok &= dalloc(c, P.ksum, NF) && dalloc(c, P.kvsum, NF) && dalloc(c, P.alpha, NF) && dalloc(c, P.k0, NF);
+    ok &= dalloc(c, P.id_c, NF) && dalloc(c, P.id_s, NF) && dalloc(c, P.nnf, NF) && dalloc(c, P.nnb, NF);
+    ok &= dalloc(c, P.nbr, (size_t)NF * cap_f) && dalloc(c, P.bnbr, (size_t)NF * cap_b);
+    ok &= dalloc(c, P.feat, (size_t)NF * 4);
+    ok &= dalloc(c, P.cell_count, NC) && dalloc(c, P.cell_start, NC + 1);
+    ok &= dalloc(c, P.key_tmp, NF) && dalloc(c, P.slot_tmp, NF) && dalloc(c, P.sid_tmp, NF) &&
+          dalloc(c, P.src_tmp, NF) && dalloc(c, P.cell_tmp, NF);
+    int64_t NBa = std::max<int64_t>(NB, 1);
+    ok &= dalloc(c, P.bx_o, NBa) && dalloc(c, P.bv_o, NBa) && dalloc(c, P.br0, NBa) && dalloc(c, P.bbody, NBa);
+    ok &= dalloc(c, P.bpos_s, NBa) && dalloc(c, P.bvel_s, NBa) && dalloc(c, P.bid_s, NBa) &&
+          dalloc(c, P.bbody_s, NBa);
+    ok &= dalloc(c, P.bcell_count, NC) && dalloc(c, P.bcell_start, NC + 1);
+    ok &= dalloc(c, P.bkey_tmp, NBa) && dalloc(c, P.bslot_tmp, NBa) && dalloc(c, P.bsid_tmp, NBa) &&
+          dalloc(c, P.bsrc_tmp, NBa) && dalloc(c, P.bcell_tmp, NBa);
+    ok &= dalloc(c, P.partial, std::max(nfblk, 1));
+    ok &= dalloc(c, P.body_partial, (size_t)std::max(nfblk, 1) * std::max(c->max_bodies, 1) * 6);
+    P.scan_tiles = scan_tiles_for(NC);
+    ok &= dalloc(c, P.scan_status, std::max(P.scan_tiles, 1));
+    if (!ok) return bail(fail(c, SPH_ENOMEM, "device allocation failed"));
+    P.scenes = c->d_scenes;
+    P.st = st;
+    P.fblk_scene = fbs;
+    P.bblk_scene = bbs;
+    if (cudaMallocHost(&c->h_flag, sizeof(uint32_t)) != cudaSuccess)
+        return bail(fail(c, SPH_ENOMEM, "pinned allocation failed"));
+
+    // streams used only for capture
+    if (cudaStreamCreateWithFlags(&c->cap0, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap1, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(c, SPH_ECUDA, "stream creation failed"));
+
+    // ---- upload
+    cudaStream_t s = c->stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    std::vector<SceneState> hst(n);
+    memset(hst.data(), 0, sizeof(SceneState) * n);
+    std::vector<float4> f4;
+    std::vector<float> zf;
+    std::vector<int32_t> ids;
+    std::vector<BodyDev> hb(std::max(nbodies, 1));
+    memset(hb.data(), 0, sizeof(BodyDev) * hb.size());
+    std::vector<float4> bx, bv, br;
+    std::vector<int32_t> bbody;
+    for (int sc = 0; sc < n; ++sc) {
+        const sph_scene_desc &d = descs[sc];
+        SceneDev &q = c->scenes[sc];
+        // initial CFL step from the initial velocities
+        double vmax = 0.0;
+        f4.resize(d.n_fluid);
+        for (int64_t i = 0; i < d.n_fluid; ++i)
+            f4[i] = make_float4(d.fluid_x[3 * i], d.fluid_x[3 * i + 1], d.fluid_x[3 * i + 2], 0.0f);
+        ok &= up(P.pos_c + q.f_off, f4.data(), sizeof(float4) * d.n_fluid);
+        ok &= up(P.pos_s + q.f_off, f4.data(), sizeof(float4) * d.n_fluid);
+        for (int64_t i = 0; i < d.n_fluid; ++i) {
+            float vx = d.fluid_v ? d.fluid_v[3 * i] : 0.f, vy = d.fluid_v ? d.fluid_v[3 * i + 1] : 0.f,
+                  vz = d.fluid_v ? d.fluid_v[3 * i + 2] : 0.f;
+            f4[i] = make_float4(vx, vy, vz, 0.0f);
+            vmax = std::max(vmax, std::sqrt((double)vx * vx + (double)vy * vy + (double)vz * vz));
+        }
+        ok &= up(P.vel_c + q.f_off, f4.data(), sizeof(float4) * d.n_fluid);
+        ok &= up(P.vel_s + q.f_off, f4.data(), sizeof(float4) * d.n_fluid);
+        ids.resize(d.n_fluid);
+        for (int64_t i = 0; i < d.n_fluid; ++i) ids[i] = (int32_t)i;
+        ok &= up(P.id_c + q.f_off, ids.data(), sizeof(int32_t) * d.n_fluid);
+        ok &= up(P.id_s + q.f_off, ids.data(), sizeof(int32_t) * d.n_fluid);
+        float dt0 = d.dt_max;
+        if (d.cfl > 0.0f && vmax > 0.0) dt0 = std::min(dt0, (float)(d.cfl * 2.0 * d.radius / vmax));
+        hst[sc].dt_next = dt0;
+        hst[sc].dt = dt0;
+        // boundary
+        bx.resize(d.n_boundary);
+        bv.resize(d.n_boundary);
+        br.resize(d.n_boundary);
+        bbody.resize(d.n_boundary);
+        for (int64_t b = 0; b < d.n_boundary; ++b) {
+            bx[b] = make_float4(d.boundary_x[3 * b], d.boundary_x[3 * b + 1], d.boundary_x[3 * b + 2], 0.0f);
+            bv[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            br[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            bbody[b] = d.boundary_body ? d.boundary_body[b] : -1;
+        }
+        for (int k = 0; k < d.n_bodies; ++k) {
+            const sph_rigid_desc &rd = d.bodies[k];
+            BodyDev &B = hb[q.body_off + k];
+            B.mass = rd.mass;
+            for (int a = 0; a < 3; ++a) {
+                B.inertia[a] = rd.inertia[a];
+                B.com[a] = rd.com[a];
+                B.vel[a] = rd.vel[a];
+                B.omega[a] = rd.omega[a];
+            }
+            for (int a = 0; a < 4; ++a) B.quat[a] = rd.quat[a];
+            B.scene = sc;
+            double w = rd.quat[0], x = rd.quat[1], y = rd.quat[2], z = rd.quat[3];
+            double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                              {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                              {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+            double rad = 0.0;
+            for (int64_t b = 0; b < d.n_boundary; ++b) {
+                if (bbody[b] != k) continue;
+                double dd[3] = {d.boundary_x[3 * b] - rd.com[0], d.boundary_x[3 * b + 1] - rd.com[1],
+                                d.boundary_x[3 * b + 2] - rd.com[2]};
+                double r0[3];
+                for (int a = 0; a < 3; ++a) r0[a] = R[0][a] * dd[0] + R[1][a] * dd[1] + R[2][a] * dd[2];
+                br[b] = make_float4((float)r0[0], (float)r0[1], (float)r0[2], 0.0f);
+                rad = std::max(rad, std::sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]));
+                double rw[3] = {dd[0], dd[1], dd[2]};
+                bv[b] = make_float4((float)(rd.vel[0] + rd.omega[1] * rw[2] - rd.omega[2] * rw[1]),
+                                    (float)(rd.vel[1] + rd.omega[2] * rw[0] - rd.omega[0] * rw[2]),
+                                    (float)(rd.vel[2] + rd.omega[0] * rw[1] - rd.omega[1] * rw[0]), 0.0f);
+            }
+            B.radius = rad;
+            for (int a = 0; a < 3; ++a) {
+                B.lo[a] = (double)d.domain_min[a] + rad;
+                B.hi[a] = (double)d.domain_max[a] - rad;
+            }
+        }
+        if (d.n_boundary > 0) {
+            ok &= up(P.bx_o + q.b_off, bx.data(), sizeof(float4) * d.n_boundary);
+            ok &= up(P.bv_o + q.b_off, bv.data(), sizeof(float4) * d.n_boundary);
+            ok &= up(P.br0 + q.b_off, br.data(), sizeof(float4) * d.n_boundary);
+            ok &= up(P.bbody + q.b_off, bbody.data(), sizeof(int32_t) * d.n_boundary);
+        }
+        if (!ok) break;
+    }
+    if (!ok) return bail(fail(c, SPH_ECUDA, "upload failed"));
+    Control hctl;
+    memset(&hctl, 0, sizeof hctl);
+    hctl.nscenes = n;
+    ok &= up(c->d_scenes, c->scenes.data(), sizeof(SceneDev) * n);
+    ok &= up(st, hst.data(), sizeof(SceneState) * n);
+    ok &= up(P.ctl, &hctl, sizeof hctl);
+    ok &= up(P.bodies, hb.data(), sizeof(BodyDev) * hb.size());
+    ok &= up(fbs, c->fblk_scene.data(), sizeof(int32_t) * std::max(nfblk, 0));
+    if (nbblk) ok &= up(bbs, c->bblk_scene.data(), sizeof(int32_t) * nbblk);
+    ok &= cudaMemsetAsync(P.cell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.bcell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.scan_status, 0, sizeof(uint64_t) * std::max(P.scan_tiles, 1), s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.kprev_c, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.kvprev_c, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.ksum, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.kvsum, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.alpha, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.k0, 0, sizeof(float) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.nnf, 0, sizeof(int32_t) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.nnb, 0, sizeof(int32_t) * NF, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.feat, 0, sizeof(float) * 4 * NF, s) == cudaSuccess;
+    if (!ok) return bail(fail(c, SPH_ECUDA, "upload failed"));
+
+    // ---- static boundary: grid order and pseudo-masses (moving bodies redo it per step)
+    if (nbblk) {
+        launch_key_hist(P, SORT_BOUNDARY, s);
+        launch_scan_cells(P, SORT_BOUNDARY, s);
+        launch_scatter(P, SORT_BOUNDARY, s);
+        launch_rank_gather(P, SORT_BOUNDARY, s);
+        launch_boundary_psi(P, 0, s);
+        sph_status cs = check_async(c);
+        if (cs != SPH_OK) return bail(cs);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(c, SPH_ECUDA, "create: %s", cudaGetErrorString(cudaGetLastError())));
+    sph_status gs = build_graph(c);
+    if (gs != SPH_OK) return bail(gs);
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status check_ctx(sph_ctx *c)
+{
+    if (!c) return SPH_EINVAL;
+    if (c->poisoned) return SPH_ECUDA;
+    return SPH_OK;
+}
+
+}  // namespace
+
+// ===================================================================================== ABI
+extern "C" {
+
+int32_t sph_abi_version(void) { return SPH_ABI_VERSION; }
+
+sph_status sph_create(const sph_scene_desc *scene, const sph_allocator *alloc, void *stream, sph_ctx **out)
+{
+    return create_impl(scene, 1, alloc, stream, out);
+}
+
+sph_status sph_create_batch(const sph_scene_desc *scenes, int32_t n, const sph_allocator *alloc, void *stream,
+                            sph_ctx **out)
+{
+    return create_impl(scenes, n, alloc, stream, out);
+}
+
+sph_status sph_step(sph_ctx *c, float dt)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (!std::isfinite(dt)) return fail(c, SPH_EINVAL, "dt not finite");
+    float want = dt > 0.0f ? dt : 0.0f;
+    if (want != c->last_dt) {
+        launch_set_dt(c->P, want, c->stream);
+        c->last_dt = want;
+        c->host_launches += 1;
+    }
+    if (c->graph_mode) {
+        CK(cudaGraphLaunch(c->exec, c->stream));
+    } else {
+        st = enqueue_step(c, c->stream, false);
+        if (st != SPH_OK) return st;
+    }
+    return check_async(c);
+}
+
+sph_status sph_steps(sph_ctx *c, int32_t n, float dt)
+{
+    if (n < 0) return fail(c, SPH_EINVAL, "negative step count");
+    for (int32_t k = 0; k < n; ++k) {
+        sph_status st = sph_step(c, dt);
+        if (st != SPH_OK) return st;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_synchronize(sph_ctx *c)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    Control hctl;
+    CK(cudaMemcpy(&hctl, c->P.ctl, sizeof hctl, cudaMemcpyDeviceToHost));
+    if (hctl.error)
+        return fail(c, SPH_ETIMEOUT, "a bounded device wait gave up (code %d)", hctl.error);
+    std::vector<SceneState> hs(c->nscenes);
+    CK(cudaMemcpy(hs.data(), c->P.st, sizeof(SceneState) * c->nscenes, cudaMemcpyDeviceToHost));
+    sph_status result = SPH_OK;
+    for (int s = 0; s < c->nscenes; ++s) {
+        int fresh = hs[s].flags & ~c->reported_flags[s];
+        c->reported_flags[s] |= hs[s].flags;
+        if (fresh & SPH_FLAG_NONFINITE) result = fail(c, SPH_ENUMERIC, "scene %d: non-finite state", s);
+        else if ((fresh & SPH_FLAG_OVERFLOW) && result == SPH_OK)
+            result = fail(c, SPH_EOVERFLOW, "scene %d: neighbour list capacity exceeded", s);
+        else if ((fresh & SPH_FLAG_NOCONVERGE) && result == SPH_OK)
+            result = fail(c, SPH_ENOCONVERGE, "scene %d: solver stopped at max_iter", s);
+    }
+    return result;
+}
+
+static sph_status scene_ok(sph_ctx *c, int32_t scene)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (scene < 0 || scene >= c->nscenes) return fail(c, SPH_EINVAL, "scene index %d out of range", scene);
+    return SPH_OK;
+}
+
+static sph_status read_into(sph_ctx *c, int32_t scene, int field, void *out, size_t bytes, bool boundary,
+                            int32_t on_device)
+{
+    if (!out) return SPH_OK;
+    const SceneDev &q = c->scenes[scene];
+    int64_t n = boundary ? q.nb : q.nf;
+    if (n == 0) return SPH_OK;
+    void *dst = out;
+    void *tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMallocAsync(&tmp, bytes, c->stream));
+        dst = tmp;
+    }
+    int blocks = (int)((n + 255) / 256);
+    if (boundary) k_read_boundary<<<blocks, 256, 0, c->stream>>>(c->P, scene, field, dst);
+    else k_read_fluid<<<blocks, 256, 0, c->stream>>>(c->P, scene, field, dst);
+    sph_status st = check_async(c);
+    if (st != SPH_OK) return st;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaFreeAsync(tmp, c->stream));
+    }
+    return SPH_OK;
+}
+
+sph_status sph_read_state(sph_ctx *c, int32_t scene, float *x, float *v, float *rho, float *pressure,
+                          int32_t on_device)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    size_t nf = (size_t)c->scenes[scene].nf;
+    if ((st = read_into(c, scene, 100, x, 12 * nf, false, on_device)) != SPH_OK) return st;
+    if ((st = read_into(c, scene, 101, v, 12 * nf, false, on_device)) != SPH_OK) return st;
+    if ((st = read_into(c, scene, 102, rho, 4 * nf, false, on_device)) != SPH_OK) return st;
+    if ((st = read_into(c, scene, 103, pressure, 4 * nf, false, on_device)) != SPH_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_read_field(sph_ctx *c, int32_t scene, int32_t field, void *out, int32_t on_device)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    size_t nf = (size_t)c->scenes[scene].nf, nb = (size_t)c->scenes[scene].nb;
+    size_t bytes;
+    bool boundary = false;
+    switch (field) {
+    case SPH_FIELD_V_DIV: bytes = 12 * nf; break;
+    case SPH_FIELD_FEATURES: bytes = 16 * nf; break;
+    case SPH_FIELD_PSI:
+    case SPH_FIELD_BOUNDARY_SORTED_ID:
+    case SPH_FIELD_BOUNDARY_CELL_KEY:
+        bytes = 4 * nb;
+        boundary = true;
+        break;
+    case SPH_FIELD_RHO: case SPH_FIELD_ALPHA: case SPH_FIELD_KAPPA: case SPH_FIELD_KAPPA_V:
+    case SPH_FIELD_NN_FLUID: case SPH_FIELD_NN_BOUNDARY: case SPH_FIELD_KAPPA_PREV:
+    case SPH_FIELD_KAPPA_V_PREV: case SPH_FIELD_CELL_KEY: case SPH_FIELD_SORTED_ID: case SPH_FIELD_KAPPA0:
+        bytes = 4 * nf;
+        break;
+    default: return fail(c, SPH_EINVAL, "unknown field %d", field);
+    }
+    if ((st = read_into(c, scene, field, out, bytes, boundary, on_device)) != SPH_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_write_state(sph_ctx *c, int32_t scene, const float *x, const float *v, const float *kappa_prev,
+                           const float *kappa_v_prev, int32_t on_device)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    const SceneDev &q = c->scenes[scene];
+    const int64_t nf = q.nf;
+    cudaStream_t s = c->stream;
+    int blocks = (int)((nf + 255) / 256);
+    k_unpermute_to_sorted<<<blocks, 256, 0, s>>>(c->P, scene);
+    k_sorted_to_canonical<<<blocks, 256, 0, s>>>(c->P, scene);
+    if ((st = check_async(c)) != SPH_OK) return st;
+    float *stage = nullptr;
+    auto stage_in = [&](const float *src, size_t bytes) -> const float * {
+        if (on_device) return src;
+        if (!stage && cudaMallocAsync(&stage, 12 * (size_t)nf, s) != cudaSuccess) return nullptr;
+        if (cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
+        return stage;
+    };
+    if (x) {
+        const float *d = stage_in(x, 12 * nf);
+        if (!d) return fail(c, SPH_ECUDA, "write_state staging failed");
+        k_pack3<<<blocks, 256, 0, s>>>(c->P.pos_c + q.f_off, d, nf, 0.0f);
+    }
+    if (v) {
+        const float *d = stage_in(v, 12 * nf);
+        if (!d) return fail(c, SPH_ECUDA, "write_state staging failed");
+        k_pack3<<<blocks, 256, 0, s>>>(c->P.vel_c + q.f_off, d, nf, 0.0f);
+    }
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (kappa_prev) CK(cudaMemcpyAsync(c->P.kprev_c + q.f_off, kappa_prev, 4 * nf, kind, s));
+    if (kappa_v_prev) CK(cudaMemcpyAsync(c->P.kvprev_c + q.f_off, kappa_v_prev, 4 * nf, kind, s));
+    k_scene_cfl<<<1, 256, 0, s>>>(c->P, scene);
+    if ((st = check_async(c)) != SPH_OK) return st;
+    if (stage) CK(cudaFreeAsync(stage, s));
+    CK(cudaStreamSynchronize(s));
+    return SPH_OK;
+}
+
+sph_status sph_get_stats(sph_ctx *c, int32_t scene, sph_stats *out)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    if (!out) return fail(c, SPH_EINVAL, "out is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    SceneState h;
+    CK(cudaMemcpy(&h, c->P.st + scene, sizeof h, cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof *out);
+    out->steps = h.steps;
+    out->div_iters = h.it[0];
+    out->dens_iters = h.it[1];
+    out->div_err = std::isinf(h.err[0]) ? 0.0 : h.err[0];
+    out->dens_err = std::isinf(h.err[1]) ? 0.0 : h.err[1];
+    out->div_err0 = h.err0[0];
+    out->dens_err0 = h.err0[1];
+    out->dt = h.dt;
+    out->dt_next = h.dt_next;
+    out->max_speed = std::sqrt(h.maxv2);
+    out->max_fluid_nbrs = h.max_nn_f;
+    out->max_boundary_nbrs = h.max_nn_b;
+    out->cg_iters = h.cg_it;
+    out->cg_residual = h.cg_res;
+    out->clamps = h.clamps;
+    out->flags = h.flags;
+    out->total_div_iters = h.total_it[0];
+    out->total_dens_iters = h.total_it[1];
+    return SPH_OK;
+}
+
+sph_status sph_read_bodies(sph_ctx *c, int32_t scene, double *out)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    const SceneDev &q = c->scenes[scene];
+    if (q.nbody == 0 || !out) return SPH_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<BodyDev> hb(q.nbody);
+    CK(cudaMemcpy(hb.data(), c->P.bodies + q.body_off, sizeof(BodyDev) * q.nbody, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < q.nbody; ++k) {
+        double *o = out + 19 * k;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = hb[k].com[a];
+            o[7 + a] = hb[k].vel[a];
+            o[10 + a] = hb[k].omega[a];
+            o[13 + a] = hb[k].force[a];
+            o[16 + a] = hb[k].torque[a];
+        }
+        for (int a = 0; a < 4; ++a) o[3 + a] = hb[k].quat[a];
+    }
+    return SPH_OK;
+}
+
+sph_status sph_set_mode(sph_ctx *c, int32_t graph, int32_t timing)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    c->graph_mode = graph != 0;
+    c->timing = timing != 0;
+    return SPH_OK;
+}
+
+sph_status sph_kernel_times(sph_ctx *c, sph_kernel_time *out, int32_t cap, int32_t *n, int32_t reset)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if ((st = harvest(c)) != SPH_OK) return st;
+    int32_t k = 0;
+    for (auto &kv : c->times) {
+        if (out && k < cap) {
+            memset(out[k].name, 0, sizeof out[k].name);
+            strncpy(out[k].name, kv.first.c_str(), sizeof out[k].name - 1);
+            out[k].launches = kv.second.first;
+            out[k].total_ms = kv.second.second;
+        }
+        ++k;
+    }
+    if (n) *n = k;
+    if (reset) c->times.clear();
+    return SPH_OK;
+}
+
+sph_status sph_launch_count(sph_ctx *c, int64_t *out)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (!out) return fail(c, SPH_EINVAL, "out is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    Control h;
+    CK(cudaMemcpy(&h, c->P.ctl, sizeof h, cudaMemcpyDeviceToHost));
+    *out = h.launches;
+    return SPH_OK;
+}
+
+const char *sph_status_string(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_EINVAL: return "invalid argument";
+    case SPH_ENOMEM: return "out of memory";
+    case SPH_ECUDA: return "CUDA error";
+    case SPH_ENOCONVERGE: return "solver did not converge";
+    case SPH_ETIMEOUT: return "device wait timed out";
+    case SPH_ENUMERIC: return "non-finite state";
+    case SPH_EOVERFLOW: return "neighbour list overflow";
+    }
+    return "unknown status";
+}
+
+const char *sph_last_error(const sph_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void sph_destroy(sph_ctx *c)
+{
+    if (!c) return;
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (auto &a : c->allocs) {
+        if (c->use_alloc) c->alloc.free(c->alloc.user, a.p, a.bytes, (void *)c->stream);
+        else cudaFree(a.p);
+    }
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->cap0) cudaStreamDestroy(c->cap0);
+    if (c->cap1) cudaStreamDestroy(c->cap1);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,640 @@
+// sph_fluid.cu -- per-particle sweeps of the DFSPH step.
+//
+// One thread owns one fluid particle in grid order.  The density sweep walks the 27-cell
+// neighbourhood (9 contiguous index ranges) once per step, applies the float neighbour
+// predicate and records each neighbour's index in a k-major list; every later sweep of
+// the step (divergence and density Jacobi passes, non-pressure forces, warm starts)
+// gathers through that list.  The solvers' error sums are accumulated per block in FP64
+// and reduced in a fixed order by the last block of each scene, which also decides the
+// loop condition on the device (CUDA graph conditional node).
+#include "sph_internal.cuh"
+
+#include <math_constants.h>
+
+namespace sph {
+
+namespace {
+
+__device__ __forceinline__ void count_launch(Control *ctl)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
+}
+
+// Cubic spline (Sec. 3.2 with h = 4r, Sec. 5): W = sigma w(q), grad W = kgrad g(q) x/|x|.
+__device__ __forceinline__ float spline_w(float q)
+{
+    if (q <= 0.5f) return fmaf(6.0f * q, q * q, fmaf(-6.0f * q, q, 1.0f));
+    float t = fmaxf(1.0f - q, 0.0f);
+    return 2.0f * t * t * t;
+}
+// grad W_ij = factor * x_ij; zero for coincident particles.
+__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
+{
+    if (!(r2 > 0.0f)) return 0.0f;
+    float rinv = rsqrtf(r2);
+    float q = r2 * rinv * sc.inv_h;
+    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
+    return sc.kgrad * g * rinv;
+}
+
+__device__ __forceinline__ void set_w(float4 *p, int64_t i, float w)
+{
+    reinterpret_cast<float *>(p + i)[3] = w;
+}
+
+struct BlockCtx {
+    const SceneDev *sc;
+    SceneState *st;
+    int64_t i;
+    bool valid;
+};
+
+__device__ __forceinline__ BlockCtx fluid_ctx(const Ptrs &P)
+{
+    BlockCtx c;
+    int32_t s = P.fblk_scene[blockIdx.x];
+    c.sc = &P.scenes[s];
+    c.st = &P.st[s];
+    int64_t local = (int64_t)(blockIdx.x - c.sc->fblk_first) * kBlock + threadIdx.x;
+    c.valid = local < c.sc->nf;
+    c.i = c.sc->f_off + local;
+    return c;
+}
+
+__device__ __forceinline__ bool solver_active(const SceneDev &sc, const SceneState &st, int s)
+{
+    if (s == 0 && !sc.div_on) return false;
+    int it = st.it[s];
+    if (it >= sc.max_it[s]) return false;
+    return it < sc.min_it[s] || st.err[s] > (double)sc.eta[s];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Fixed-order block sum of one double per thread (deterministic).
+__device__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kBlock / 32; ++k) t += sh[k];
+    return t;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------------------------
+// Step begin: per-scene counters and the step size.
+__global__ void k_step_begin(Ptrs P)
+{
+    count_launch(P.ctl);
+    int s = threadIdx.x + blockIdx.x * blockDim.x;
+    if (s == 0) {
+        P.ctl->passb_counter = 0;
+        P.ctl->loop_guard = 0;
+    }
+    if (s >= P.nscenes) return;
+    const SceneDev &sc = P.scenes[s];
+    SceneState &st = P.st[s];
+    float od = P.ctl->dt_override;
+    st.dt = od > 0.0f ? od : (sc.cfl > 0.0f ? st.dt_next : sc.dt_max);
+    for (int k = 0; k < 2; ++k) {
+        st.it[k] = 0;
+        st.pending[k] = 0;
+        st.err[k] = CUDART_INF;
+        st.err0[k] = 0.0;
+    }
+    st.counter = 0;
+    st.max_nn_f = 0;
+    st.max_nn_b = 0;
+    st.maxv2 = 0.0f;
+}
+
+// ------------------------------------------------------------------------------------
+// Density (Eq. density + Sec. 3.5 boundary term), DFSPH alpha, neighbour lists, and the
+// gate of the divergence warm start (D rho/Dt with the velocities at step start).
+__global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
+{
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    const SceneDev &sc = *c.sc;
+    int nn_f = 0, nn_b = 0;
+    if (c.valid) {
+        const int64_t i = c.i, NF = P.NF;
+        const float4 pi = P.pos_s[i];
+        const float4 vi = P.vel_s[i];
+        const int32_t cx = cell_coord(pi.x, sc.origin[0], sc.cell, sc.dims[0]);
+        const int32_t cy = cell_coord(pi.y, sc.origin[1], sc.cell, sc.dims[1]);
+        const int32_t cz = cell_coord(pi.z, sc.origin[2], sc.cell, sc.dims[2]);
+        const int32_t x0 = max(cx - 1, 0), x1 = min(cx + 1, sc.dims[0] - 1);
+        const float h2 = sc.h2;
+        const bool gate = sc.warm != 0 && sc.div_on;
+        float w_sum = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, s2 = 0.0f, div_f = 0.0f;
+        for (int32_t dz = -1; dz <= 1; ++dz) {
+            const int32_t z = cz + dz;
+            if (z < 0 || z >= sc.dims[2]) continue;
+            for (int32_t dy = -1; dy <= 1; ++dy) {
+                const int32_t y = cy + dy;
+                if (y < 0 || y >= sc.dims[1]) continue;
+                const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
+                const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
+                for (uint32_t j = jb; j < je; ++j) {
+                    if ((int64_t)j == i) continue;
+                    const float4 pj = P.pos_s[j];
+                    float dx, dy2, dz2;
+                    const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
+                    if (!(d2 < h2)) continue;
+                    if (nn_f < sc.cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
+                    ++nn_f;
+                    const float r = sqrtf(d2);
+                    w_sum += spline_w(r * sc.inv_h);
+                    const float f = grad_factor(sc, d2);
+                    const float gx = f * dx, gy = f * dy2, gz = f * dz2;
+                    s1x += gx; s1y += gy; s1z += gz;
+                    s2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, s2)));
+                    if (gate) {
+                        const float4 vj = P.vel_s[j];
+                        div_f += (vi.x - vj.x) * gx + (vi.y - vj.y) * gy + (vi.z - vj.z) * gz;
+                    }
+                }
+            }
+        }
+        float rho = sc.m * sc.sigma * (1.0f + w_sum);
+        s1x *= sc.m; s1y *= sc.m; s1z *= sc.m;
+        s2 *= sc.m * sc.m;
+        float div = sc.m * div_f;
+        if (sc.nb > 0) {
+            float wb = 0.0f, divb = 0.0f;
+            for (int32_t dz = -1; dz <= 1; ++dz) {
+                const int32_t z = cz + dz;
+                if (z < 0 || z >= sc.dims[2]) continue;
+                for (int32_t dy = -1; dy <= 1; ++dy) {
+                    const int32_t y = cy + dy;
+                    if (y < 0 || y >= sc.dims[1]) continue;
+                    const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
+                    const uint32_t jb = P.bcell_start[row + x0], je = P.bcell_start[row + x1 + 1];
+                    for (uint32_t b = jb; b < je; ++b) {
+                        const float4 pb = P.bpos_s[b];
+                        float dx, dy2, dz2;
+                        const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
+                        if (!(d2 < h2)) continue;
+                        if (nn_b < sc.cap_b) P.bnbr[(int64_t)nn_b * NF + i] = (int32_t)b;
+                        ++nn_b;
+                        const float r = sqrtf(d2);
+                        const float psi = pb.w;
+                        wb += psi * spline_w(r * sc.inv_h);
+                        const float f = psi * grad_factor(sc, d2);
+                        const float gx = f * dx, gy = f * dy2, gz = f * dz2;
+                        s1x += gx; s1y += gy; s1z += gz;
+                        if (gate) {
+                            float4 vb = sc.has_moving ? P.bvel_s[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            divb += (vi.x - vb.x) * gx + (vi.y - vb.y) * gy + (vi.z - vb.z) * gz;
+                        }
+                    }
+                }
+            }
+            rho += sc.sigma * wb;
+            div += divb;
+        }
+        const float den = fmaf(s1x, s1x, fmaf(s1y, s1y, fmaf(s1z, s1z, s2)));
+        const float alpha = den > sc.eps_alpha ? rho / den : 0.0f;
+        P.alpha[i] = alpha;
+        set_w(P.vel_s, i, rho);
+        P.nnf[i] = min(nn_f, sc.cap_f);
+        P.nnb[i] = min(nn_b, sc.cap_b);
+        float kv0 = 0.0f;
+        if (gate && div > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
+        P.kvsum[i] = kv0;
+        set_w(P.pos_s, i, kv0 / rho);
+    }
+    int mf = warp_max(nn_f), mb = warp_max(nn_b);
+    if ((threadIdx.x & 31) == 0) {
+        if (mf > 0) atomicMax(&c.st->max_nn_f, mf);
+        if (mb > 0) atomicMax(&c.st->max_nn_b, mb);
+        if (mf > sc.cap_f || mb > sc.cap_b) atomicOr(&c.st->flags, 1);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// D rho_i/Dt = sum_j m (v_i - v_j).grad W_ij + sum_b Psi_b (v_i - v_b).grad W_ib
+// (SPH divergence of Sec. 3.2 in the continuity equation, boundary per Sec. 3.5).
+__device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi,
+                                         float4 vi, const float4 *__restrict__ V)
+{
+    const int64_t NF = P.NF;
+    const int nn = P.nnf[i];
+    float acc = 0.0f;
+    for (int k = 0; k < nn; ++k) {
+        const int32_t j = P.nbr[(int64_t)k * NF + i];
+        const float4 pj = P.pos_s[j];
+        const float4 vj = V[j];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        acc = fmaf(f, (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz, acc);
+    }
+    acc *= sc.m;
+    const int nb = P.nnb[i];
+    float accb = 0.0f;
+    for (int k = 0; k < nb; ++k) {
+        const int32_t b = P.bnbr[(int64_t)k * NF + i];
+        const float4 pb = P.bpos_s[b];
+        const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
+        const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float ux = vi.x, uy = vi.y, uz = vi.z;
+        if (sc.has_moving) {
+            const float4 vb = P.bvel_s[b];
+            ux -= vb.x; uy -= vb.y; uz -= vb.z;
+        }
+        accb = fmaf(f, ux * dx + uy * dy + uz * dz, accb);
+    }
+    return acc + accb;
+}
+
+// Pass A of a Jacobi iteration (Alg. ppe_solver "refine p"): the source term of
+// Eq. velocity_source (solver 0) or Eq. density_source with rho* (solver 1), the
+// stiffness kappa_i = alpha_i e_i / dt^(1 or 2), and the block's FP64 error partial.
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
+{
+    __shared__ double sh[kBlock / 32];
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    if (!solver_active(sc, st, S)) return;  // uniform per block
+    const float dt = st.dt;
+    double e = 0.0;
+    if (c.valid) {
+        const int64_t i = c.i;
+        const float4 *V = S == 0 ? P.vel_s : P.vel_c;
+        const float4 pi = P.pos_s[i];
+        const float4 vi = V[i];
+        const float rho = vi.w;
+        const float D = drho_dt(P, sc, i, pi, vi, V);
+        float ei, kappa;
+        if (S == 0) {
+            ei = fmaxf(D, 0.0f);
+            kappa = P.alpha[i] * ei / dt;
+            P.kvsum[i] += kappa;
+        } else {
+            ei = fmaxf(fmaf(dt, D, rho - sc.rho0), 0.0f);
+            kappa = P.alpha[i] * ei / (dt * dt);
+            P.ksum[i] += kappa;
+        }
+        set_w(P.pos_s, i, kappa / rho);
+        e = (double)ei;
+    }
+    double bsum = block_sum(e, sh);
+    if (threadIdx.x == 0) {
+        P.partial[blockIdx.x] = bsum;
+        __threadfence();
+        uint32_t prev = atomicAdd(&st.counter, 1u);
+        s_last = (prev == (uint32_t)sc.fblk_count - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last block of this scene: fixed-order sum of the scene's partials
+    __threadfence();
+    double t = 0.0;
+    const volatile double *part = P.partial;
+    for (int k = threadIdx.x; k < sc.fblk_count; k += kBlock) t += part[sc.fblk_first + k];
+    double total = block_sum(t, sh);
+    if (threadIdx.x == 0) {
+        double err = sc.nf > 0 ? total / (double)sc.nf / (double)sc.rho0 : 0.0;
+        if (S == 0) err *= (double)dt;
+        if (st.it[S] == 0) st.err0[S] = err;
+        st.err[S] = err;
+        st.pending[S] = 1;
+        st.counter = 0;
+    }
+}
+
+// Pass B (Alg. ppe_solver "update v*"): pressure acceleration of Sec. 3.3 Eq.
+// pressure_acceleration with p/rho^2 = kappa/rho, plus the boundary term of Sec. 3.5
+// Eq. rigid_pressure per unit fluid mass:
+//   v_i -= dt [ sum_j m (k_i/rho_i + k_j/rho_j) grad W_ij + sum_b Psi_b (k_i/rho_i) grad W_ib ]
+// WARM = 1 applies the warm-start kappas (no loop bookkeeping).
+template <int S, int WARM>
+__global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
+{
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    bool run = WARM ? (sc.warm != 0 && (S == 1 || sc.div_on)) : (st.pending[S] != 0);
+    if (run && c.valid) {
+        const int64_t i = c.i, NF = P.NF;
+        float4 *V = S == 0 ? P.vel_s : P.vel_c;
+        const float4 pi = P.pos_s[i];
+        const float ki = pi.w;
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        const int nn = P.nnf[i];
+        for (int k = 0; k < nn; ++k) {
+            const int32_t j = P.nbr[(int64_t)k * NF + i];
+            const float4 pj = P.pos_s[j];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
+            ax = fmaf(f, dx, ax); ay = fmaf(f, dy, ay); az = fmaf(f, dz, az);
+        }
+        ax *= sc.m; ay *= sc.m; az *= sc.m;
+        if (ki != 0.0f) {
+            const int nb = P.nnb[i];
+            float bx = 0.0f, by = 0.0f, bz = 0.0f;
+            for (int k = 0; k < nb; ++k) {
+                const int32_t b = P.bnbr[(int64_t)k * NF + i];
+                const float4 pb = P.bpos_s[b];
+                const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
+                const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                bx = fmaf(f, dx, bx); by = fmaf(f, dy, by); bz = fmaf(f, dz, bz);
+            }
+            ax = fmaf(ki, bx, ax); ay = fmaf(ki, by, ay); az = fmaf(ki, bz, az);
+        }
+        const float dt = st.dt;
+        float4 v = V[i];
+        v.x -= dt * ax; v.y -= dt * ay; v.z -= dt * az;
+        V[i] = v;
+    }
+    if (WARM) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        uint32_t prev = atomicAdd(&P.ctl->passb_counter, 1u);
+        s_last = (prev == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    // last block of the whole launch: advance the iteration counters, decide the loop
+    __threadfence();
+    uint32_t any = 0;
+    for (int s = 0; s < P.nscenes; ++s) {
+        const SceneDev &q = P.scenes[s];
+        SceneState &qs = P.st[s];
+        if (qs.pending[S]) {
+            qs.it[S] += 1;
+            qs.total_it[S] += 1;
+            qs.pending[S] = 0;
+            if (!solver_active(q, qs, S) && qs.err[S] > (double)q.eta[S]) qs.flags |= 2;
+        }
+        if (solver_active(q, qs, S)) any = 1;
+    }
+    uint32_t guard = ++P.ctl->loop_guard;
+    if (guard > 100000u) {
+        any = 0;
+        P.ctl->error = 2;
+    }
+    if (!any) P.ctl->loop_guard = 0;
+    P.ctl->loop_flag = any;
+    P.ctl->passb_counter = 0;
+    __threadfence();
+    if (use_handle) cudaGraphSetConditional(handle, any);
+}
+
+// ------------------------------------------------------------------------------------
+// Non-pressure forces (Sec. 3.3 Alg. general_algorithm, Sec. 4.2: gravity, then
+// viscosity): v* = v + dt (g + (mu/rho_i) lap v_i) with Eq. lap
+//   lap v_i = 2(d+2) sum_j (m/rho_j) (v_ij . x_ij)/(|x_ij|^2 + 0.01 h^2) grad W_ij,
+// or XSPH smoothing c sum_j (m/rho_j)(v_j - v_i) W_ij.  Writes v* to the canonical
+// velocity array and clears the density-solve stiffness sum.
+__global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
+{
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    if (!c.valid) return;
+    const SceneDev &sc = *c.sc;
+    const int64_t i = c.i, NF = P.NF;
+    const float dt = c.st->dt;
+    const float4 pi = P.pos_s[i];
+    const float4 vi = P.vel_s[i];
+    const float rho_i = vi.w;
+    float ax = sc.g[0], ay = sc.g[1], az = sc.g[2];
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    if (sc.visc_mode == 1 || sc.visc_mode == 2) {
+        const int nn = P.nnf[i];
+        const float reg = 0.01f * sc.h2;
+        for (int k = 0; k < nn; ++k) {
+            const int32_t j = P.nbr[(int64_t)k * NF + i];
+            const float4 pj = P.pos_s[j];
+            const float4 vj = P.vel_s[j];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (sc.visc_mode == 1) {
+                const float f = grad_factor(sc, r2);
+                const float s = f * (ux * dx + uy * dy + uz * dz) / ((r2 + reg) * vj.w);
+                sx = fmaf(s, dx, sx); sy = fmaf(s, dy, sy); sz = fmaf(s, dz, sz);
+            } else {
+                const float w = spline_w(sqrtf(r2) * sc.inv_h) / vj.w;
+                sx = fmaf(-w, ux, sx); sy = fmaf(-w, uy, sy); sz = fmaf(-w, uz, sz);
+            }
+        }
+    }
+    float4 v = vi;
+    if (sc.visc_mode == 1) {
+        const float k = 10.0f * sc.mu * sc.m / rho_i;
+        v.x += dt * fmaf(k, sx, ax); v.y += dt * fmaf(k, sy, ay); v.z += dt * fmaf(k, sz, az);
+    } else if (sc.visc_mode == 2) {
+        const float k = sc.xsph * sc.m * sc.sigma;
+        v.x += fmaf(dt, ax, k * sx); v.y += fmaf(dt, ay, k * sy); v.z += fmaf(dt, az, k * sz);
+    } else {
+        v.x += dt * ax; v.y += dt * ay; v.z += dt * az;
+    }
+    v.w = rho_i;
+    P.vel_c[i] = v;
+    P.ksum[i] = 0.0f;
+    P.k0[i] = 0.0f;
+    set_w(P.pos_s, i, 0.0f);
+}
+
+// Warm start of the constant-density solve: the predicted deviation rho* - rho0 with
+// v* gates half the previous step's stiffness (kept as kappa dt^2); the learned mode
+// stores the network's input features instead (rho/rho0 - 1, dt Drho/Dt/rho0,
+// (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.
+__global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
+{
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    if (!c.valid) return;
+    const SceneDev &sc = *c.sc;
+    if (sc.warm == 0) return;
+    const int64_t i = c.i;
+    const float dt = c.st->dt;
+    const float4 pi = P.pos_s[i];
+    const float4 vi = P.vel_c[i];
+    const float rho = vi.w;
+    const float D = drho_dt(P, sc, i, pi, vi, P.vel_c);
+    const float dev = fmaf(dt, D, rho - sc.rho0);
+    float k0 = 0.0f;
+    if (sc.warm == 1) {
+        if (dev > 0.0f) k0 = 0.5f * P.kprev_s[i] / (dt * dt);
+    } else if (P.have_mlp) {
+        const float kref = 9.81f * sc.h;
+        float4 f;
+        f.x = rho / sc.rho0 - 1.0f;
+        f.y = dt * D / sc.rho0;
+        f.z = (float)(P.nnf[i] + P.nnb[i]) / 33.0f;
+        f.w = P.kprev_s[i] / (dt * dt) / kref;
+        reinterpret_cast<float4 *>(P.feat)[i] = f;
+        k0 = dev > 0.0f ? 1.0f : 0.0f;   // gate; the network kernel replaces it
+    }
+    P.k0[i] = k0;
+    P.ksum[i] = k0;
+    set_w(P.pos_s, i, k0 / rho);
+}
+
+// Advect (Sec. 3.3 Alg. general_algorithm, symplectic Euler): x = x + dt v*, written
+// back in grid order as the next step's canonical state, with the warm-start memory.
+__global__ void __launch_bounds__(kBlock) k_advect(Ptrs P)
+{
+    count_launch(P.ctl);
+    BlockCtx c = fluid_ctx(P);
+    float v2 = 0.0f;
+    bool bad = false;
+    if (c.valid) {
+        const int64_t i = c.i;
+        const float dt = c.st->dt;
+        const float4 v = P.vel_c[i];
+        float4 p = P.pos_s[i];
+        p.x = fmaf(dt, v.x, p.x);
+        p.y = fmaf(dt, v.y, p.y);
+        p.z = fmaf(dt, v.z, p.z);
+        p.w = 0.0f;
+        P.pos_c[i] = p;
+        P.id_c[i] = P.id_s[i];
+        P.kprev_c[i] = P.ksum[i] * dt * dt;
+        P.kvprev_c[i] = P.kvsum[i] * dt;
+        v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+        bad = !isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z) || !isfinite(v2);
+    }
+    float m = v2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (m > 0.0f && isfinite(m)) atomicMax(reinterpret_cast<int *>(&c.st->maxv2), __float_as_int(m));
+        if (anybad) atomicOr(&c.st->flags, 4);
+    }
+}
+
+// Step end: CFL step for the next step (not in the paper: dt = min(dt_max, cfl 2r /
+// max|v|)), counters, and the rigid bodies (symplectic Euler with a renormalised
+// quaternion; weak coupling: bodies move only between fluid steps, Sec. 2.2 / 6).
+__global__ void k_step_end(Ptrs P)
+{
+    count_launch(P.ctl);
+    int t = threadIdx.x;
+    for (int s = t; s < P.nscenes; s += blockDim.x) {
+        const SceneDev &sc = P.scenes[s];
+        SceneState &st = P.st[s];
+        float vm = sqrtf(st.maxv2);
+        float dt = sc.dt_max;
+        if (sc.cfl > 0.0f && vm > 0.0f) dt = fminf(dt, sc.cfl * sc.two_r / vm);
+        st.dt_next = dt;
+        st.steps += 1;
+    }
+    for (int k = t; k < P.nbodies_total; k += blockDim.x) {
+        BodyDev &B = P.bodies[k];
+        const SceneDev &sc = P.scenes[B.scene];
+        const double dt = (double)P.st[B.scene].dt;
+        for (int a = 0; a < 3; ++a) B.vel[a] += dt * (B.force[a] / B.mass + (double)sc.g[a]);
+        for (int a = 0; a < 3; ++a) B.com[a] += dt * B.vel[a];
+        double w = B.quat[0], x = B.quat[1], y = B.quat[2], z = B.quat[3];
+        double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                          {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                          {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        double Iw[3][3], Ii[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int e = 0; e < 3; ++e) {
+                Iw[a][e] = 0.0;
+                Ii[a][e] = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    Iw[a][e] += R[a][q] * B.inertia[q] * R[e][q];
+                    Ii[a][e] += R[a][q] / B.inertia[q] * R[e][q];
+                }
+            }
+        double o[3] = {B.omega[0], B.omega[1], B.omega[2]};
+        double L[3];
+        for (int a = 0; a < 3; ++a) L[a] = Iw[a][0] * o[0] + Iw[a][1] * o[1] + Iw[a][2] * o[2];
+        double rhs[3] = {B.torque[0] - (o[1] * L[2] - o[2] * L[1]),
+                         B.torque[1] - (o[2] * L[0] - o[0] * L[2]),
+                         B.torque[2] - (o[0] * L[1] - o[1] * L[0])};
+        for (int a = 0; a < 3; ++a) B.omega[a] += dt * (Ii[a][0] * rhs[0] + Ii[a][1] * rhs[1] + Ii[a][2] * rhs[2]);
+        double ox = B.omega[0], oy = B.omega[1], oz = B.omega[2];
+        double dw = 0.5 * (-ox * x - oy * y - oz * z);
+        double dx = 0.5 * (ox * w + oy * z - oz * y);
+        double dy = 0.5 * (oy * w + oz * x - ox * z);
+        double dz = 0.5 * (oz * w + ox * y - oy * x);
+        w += dt * dw; x += dt * dx; y += dt * dy; z += dt * dz;
+        double nq = sqrt(w * w + x * x + y * y + z * z);
+        B.quat[0] = w / nq; B.quat[1] = x / nq; B.quat[2] = y / nq; B.quat[3] = z / nq;
+        // no contact model (the paper delegates contact to PyBullet): the bounding sphere
+        // is clamped inside the domain, and each clamp is counted
+        for (int a = 0; a < 3; ++a) {
+            if (B.com[a] < B.lo[a]) {
+                B.com[a] = B.lo[a];
+                if (B.vel[a] < 0.0) B.vel[a] = 0.0;
+                atomicAdd(&P.st[B.scene].clamps, 1);
+            }
+            if (B.com[a] > B.hi[a]) {
+                B.com[a] = B.hi[a];
+                if (B.vel[a] > 0.0) B.vel[a] = 0.0;
+                atomicAdd(&P.st[B.scene].clamps, 1);
+            }
+        }
+    }
+}
+
+__global__ void k_set_dt(Control *ctl, float dt)
+{
+    count_launch(ctl);
+    ctl->dt_override = dt;
+}
+
+}  // namespace
+
+void launch_step_begin(const Ptrs &P, cudaStream_t s)
+{
+    int t = P.nscenes < 1024 ? ((P.nscenes + 31) / 32) * 32 : 1024;
+    int b = (P.nscenes + t - 1) / t;
+    k_step_begin<<<b, t, 0, s>>>(P);
+}
+void launch_density_alpha(const Ptrs &P, cudaStream_t s) { k_density_alpha<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_pass_a(const Ptrs &P, int solver, cudaStream_t s)
+{
+    if (solver == 0) k_pass_a<0><<<P.nfblk, kBlock, 0, s>>>(P);
+    else k_pass_a<1><<<P.nfblk, kBlock, 0, s>>>(P);
+}
+void launch_pass_b(const Ptrs &P, int solver, int warm, cudaGraphConditionalHandle h, int use_handle,
+                   cudaStream_t s)
+{
+    if (solver == 0) {
+        if (warm) k_pass_b<0, 1><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+        else k_pass_b<0, 0><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+    } else {
+        if (warm) k_pass_b<1, 1><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+        else k_pass_b<1, 0><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+    }
+}
+void launch_nonpressure(const Ptrs &P, cudaStream_t s) { k_nonpressure<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_warm_density(const Ptrs &P, cudaStream_t s) { k_warm_density<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_advect(const Ptrs &P, cudaStream_t s) { k_advect<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_step_end(const Ptrs &P, cudaStream_t s) { k_step_end<<<1, 128, 0, s>>>(P); }
+void launch_set_dt(const Ptrs &P, float dt, cudaStream_t s) { k_set_dt<<<1, 1, 0, s>>>(P.ctl, dt); }
+
+}  // namespace sph

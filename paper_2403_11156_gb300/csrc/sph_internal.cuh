@@ -1,0 +1,184 @@
+// sph_internal.cuh -- device-side data layout and kernel launchers of the DFSPH pipeline.
+//
+// Layout in HBM (all scenes of a context concatenated; a scene is a contiguous range):
+//   fluid, current sorted order  pos_s  float4 (x, y, z, kappa/rho of the current sweep)
+//                                vel_s  float4 (v, rho)
+//   fluid, canonical order       pos_c, vel_c (same packing), kprev_c, kvprev_c, id_c
+//   neighbour lists              nbr[k * NF + i], bnbr[k * NF + i]  (k-major: coalesced)
+//   boundary, original order     bx_o float4 (x, 0), bv_o float4, br0 float4, bbody int32
+//   boundary, sorted order       bpos_s float4 (x, Psi), bvel_s float4 (v_b, 0)
+// "Canonical" is the sorted order of the previous step: the reorder gathers canonical ->
+// sorted, the step ends by writing the advected state back into the canonical arrays.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int kBlock = 128;           // threads per particle block
+constexpr int kMaxBodies = 64;
+
+// Per-scene constants (device, read-only during a step).
+struct SceneDev {
+    int64_t f_off, nf;                // fluid range
+    int64_t b_off, nb;                // boundary range
+    int64_t c_off;                    // first global cell of this scene's grid
+    int32_t dims[3];
+    int32_t ncell;
+    float origin[3];
+    float cell;
+    float h, h2, inv_h;
+    float m;                          // particle mass rho0 (2r)^3
+    float rho0;
+    float sigma;                      // W(0) = 8/(pi h^3)
+    float kgrad;                      // 48/(pi h^4): grad W = kgrad g(q) x/|x|
+    float eps_alpha;                  // alpha guard on the denominator
+    float mu;                         // nu rho0
+    float xsph;
+    float g[3];
+    float eta[2];                     // [0] divergence, [1] density
+    float dt_max, cfl, two_r;
+    int32_t min_it[2], max_it[2];
+    int32_t visc_mode, warm, div_on, has_moving;
+    int32_t body_off, nbody;
+    int32_t fblk_first, fblk_count;   // fluid particle blocks of this scene
+    int32_t bblk_first, bblk_count;   // boundary particle blocks
+    int32_t cap_f, cap_b;             // neighbour list capacities
+    float cg_tol;
+    int32_t cg_max;
+};
+
+// Per-scene mutable state (device).
+struct SceneState {
+    float dt, dt_next;
+    float maxv2;                      // written via atomicMax on the bit pattern
+    int32_t flags;
+    int32_t it[2];                    // iterations of the current step
+    int32_t pending[2];               // pass A ran in this loop iteration
+    double err[2], err0[2];
+    uint32_t counter;                 // last-block counter of pass A
+    int32_t max_nn_f, max_nn_b;
+    int32_t cg_it;
+    float cg_res;
+    int32_t clamps;
+    int64_t steps;
+    int64_t total_it[2];
+};
+
+// Rigid body state (device, FP64).
+struct BodyDev {
+    double mass, inertia[3];
+    double com[3], quat[4], vel[3], omega[3];
+    double force[3], torque[3];
+    double radius;                    // bounding sphere of its boundary particles
+    double lo[3], hi[3];              // clamp box of the centre of mass
+    int32_t scene;
+    int32_t pad;
+};
+
+// Context-wide control words (device).
+struct Control {
+    uint32_t passb_counter;           // last-block counter of pass B (all scenes)
+    uint32_t loop_flag;               // host-readable copy of the loop condition
+    uint32_t loop_guard;              // iterations of the current loop
+    uint32_t pad0;
+    int64_t launches;                 // kernel launches counted on the device
+    float dt_override;                // > 0: fixed step for all scenes
+    int32_t nscenes;
+    int32_t scan_tile_counter;        // decoupled look-back tile ticket
+    int32_t scan_done;
+    uint32_t scan_epoch;
+    int32_t error;                    // bounded-wait failures
+};
+
+struct Ptrs {
+    const SceneDev *scenes;
+    SceneState *st;
+    Control *ctl;
+    BodyDev *bodies;
+    const int32_t *fblk_scene;        // scene of each fluid block
+    const int32_t *bblk_scene;        // scene of each boundary block
+    int32_t nfblk, nbblk, nscenes, nbodies_total;
+    int64_t NF, NB, NC;               // totals: fluid, boundary, cells
+    // fluid
+    float4 *pos_s, *vel_s, *pos_c, *vel_c;
+    float *kprev_c, *kvprev_c, *kprev_s, *kvprev_s;
+    float *ksum, *kvsum, *alpha, *k0;
+    int32_t *id_c, *id_s;
+    int32_t *nnf, *nnb;
+    int32_t *nbr, *bnbr;
+    float *feat;                      // [NF][4]
+    // grid scratch (fluid)
+    uint32_t *cell_count, *cell_start;
+    uint32_t *key_tmp, *slot_tmp;
+    uint32_t *sid_tmp, *src_tmp, *cell_tmp;
+    // boundary
+    float4 *bx_o, *bv_o, *br0;
+    int32_t *bbody;
+    float4 *bpos_s, *bvel_s;
+    int32_t *bid_s;
+    int32_t *bbody_s;
+    uint32_t *bcell_count, *bcell_start;
+    uint32_t *bkey_tmp, *bslot_tmp, *bsid_tmp, *bsrc_tmp, *bcell_tmp;
+    // reductions
+    double *partial;                  // [nfblk]
+    double *body_partial;             // [nfblk][6] per body pass
+    uint64_t *scan_status;            // [tiles]
+    int32_t scan_tiles;
+    // implicit viscosity CG
+    float4 *cg_r, *cg_p, *cg_ap;
+    double *cg_dots;                  // per-block partials [nfblk][2]
+    double *cg_scal;                  // per-scene scalars [S][4]: rr, pAp, bb, alpha...
+    // network
+    const float *mlp_w;               // device weights (float master copy)
+    int32_t have_mlp;
+};
+
+// ------------------------------------------------------------------ grid (sph_grid.cu)
+// Cell coordinate under the float contract: clamp(floor((x - o)/c), 0, n-1).
+__device__ __forceinline__ int32_t cell_coord(float x, float o, float c, int32_t n)
+{
+    float t = __fdiv_rn(__fsub_rn(x, o), c);
+    if (!(t > 0.0f)) return 0;
+    if (t >= (float)(n - 1)) return n - 1;
+    return (int32_t)floorf(t);
+}
+
+// Neighbour predicate contract: d2 = ((dx*dx)+(dy*dy))+(dz*dz) in float, no FMA, d2 < h2.
+__device__ __forceinline__ float pred_d2(float4 a, float4 b, float &dx, float &dy, float &dz)
+{
+    dx = __fsub_rn(a.x, b.x);
+    dy = __fsub_rn(a.y, b.y);
+    dz = __fsub_rn(a.z, b.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+enum SortWhat { SORT_FLUID = 0, SORT_BOUNDARY = 1 };
+
+void launch_key_hist(const Ptrs &P, SortWhat what, cudaStream_t s);
+void launch_scan_cells(const Ptrs &P, SortWhat what, cudaStream_t s);
+void launch_scatter(const Ptrs &P, SortWhat what, cudaStream_t s);
+void launch_rank_gather(const Ptrs &P, SortWhat what, cudaStream_t s);
+void launch_scan(uint32_t *count, uint32_t *start, int64_t n, uint64_t *status, int32_t tiles,
+                 Control *ctl, cudaStream_t s);
+int32_t scan_tiles_for(int64_t n);
+
+// ------------------------------------------------------------------ fluid (sph_fluid.cu)
+void launch_step_begin(const Ptrs &P, cudaStream_t s);
+void launch_density_alpha(const Ptrs &P, cudaStream_t s);
+void launch_pass_a(const Ptrs &P, int solver, cudaStream_t s);
+void launch_pass_b(const Ptrs &P, int solver, int warm, cudaGraphConditionalHandle h,
+                   int use_handle, cudaStream_t s);
+void launch_nonpressure(const Ptrs &P, cudaStream_t s);
+void launch_warm_density(const Ptrs &P, cudaStream_t s);
+void launch_advect(const Ptrs &P, cudaStream_t s);
+void launch_step_end(const Ptrs &P, cudaStream_t s);
+void launch_set_dt(const Ptrs &P, float dt, cudaStream_t s);
+
+// ------------------------------------------------------------------ rigid (sph_rigid.cu)
+void launch_boundary_update(const Ptrs &P, cudaStream_t s);
+void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);
+void launch_body_force(const Ptrs &P, int max_bodies, cudaStream_t s);
+
+}  // namespace sph

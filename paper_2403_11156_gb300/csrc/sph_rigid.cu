@@ -1,0 +1,198 @@
+// sph_rigid.cu -- Akinci boundary handling and two-way rigid coupling (Sec. 3.5).
+//
+//  * boundary pseudo-mass Psi_b = rho0 / sum_k W_bk over boundary neighbours, the
+//    particle itself included (all walls and bodies count);
+//  * moving-body boundary particles follow their body: x_b = com + R r0_b,
+//    v_b = v + omega x (R r0_b);
+//  * the reaction of Eq. rigid_pressure_symmetric: F_{b<-i} = m Psi_b (kappa_i/rho_i)
+//    grad W_ib with the step's total applied kappa (divergence + density solves), summed
+//    per body with its torque in FP64 and reduced in a fixed order.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+__device__ __forceinline__ void count_launch(Control *ctl)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
+}
+
+__device__ __forceinline__ float spline_w(float q)
+{
+    if (q <= 0.5f) return fmaf(6.0f * q, q * q, fmaf(-6.0f * q, q, 1.0f));
+    float t = fmaxf(1.0f - q, 0.0f);
+    return 2.0f * t * t * t;
+}
+
+__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
+{
+    if (!(r2 > 0.0f)) return 0.0f;
+    float rinv = rsqrtf(r2);
+    float q = r2 * rinv * sc.inv_h;
+    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
+    return sc.kgrad * g * rinv;
+}
+
+// Boundary particles of moving bodies follow their body (original order).
+__global__ void __launch_bounds__(kBlock) k_boundary_update(Ptrs P)
+{
+    count_launch(P.ctl);
+    const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
+    if (!sc.has_moving) return;
+    int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
+    if (local >= sc.nb) return;
+    int64_t b = sc.b_off + local;
+    int32_t k = P.bbody[b];
+    if (k < 0) return;
+    const BodyDev &B = P.bodies[sc.body_off + k];
+    double w = B.quat[0], x = B.quat[1], y = B.quat[2], z = B.quat[3];
+    float4 r0 = P.br0[b];
+    double rx = r0.x, ry = r0.y, rz = r0.z;
+    double wx = (1 - 2 * (y * y + z * z)) * rx + 2 * (x * y - w * z) * ry + 2 * (x * z + w * y) * rz;
+    double wy = 2 * (x * y + w * z) * rx + (1 - 2 * (x * x + z * z)) * ry + 2 * (y * z - w * x) * rz;
+    double wz = 2 * (x * z - w * y) * rx + 2 * (y * z + w * x) * ry + (1 - 2 * (x * x + y * y)) * rz;
+    P.bx_o[b] = make_float4((float)(B.com[0] + wx), (float)(B.com[1] + wy), (float)(B.com[2] + wz), 0.0f);
+    P.bv_o[b] = make_float4((float)(B.vel[0] + (B.omega[1] * wz - B.omega[2] * wy)),
+                            (float)(B.vel[1] + (B.omega[2] * wx - B.omega[0] * wz)),
+                            (float)(B.vel[2] + (B.omega[0] * wy - B.omega[1] * wx)), 0.0f);
+}
+
+// Psi_b = rho0 / (sigma (1 + sum_k w(q_bk)))  (grid order; stored in bpos_s.w)
+__global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving)
+{
+    count_launch(P.ctl);
+    const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
+    if (only_moving && !sc.has_moving) return;
+    int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
+    if (local >= sc.nb) return;
+    int64_t b = sc.b_off + local;
+    const float4 pb = P.bpos_s[b];
+    const int32_t cx = cell_coord(pb.x, sc.origin[0], sc.cell, sc.dims[0]);
+    const int32_t cy = cell_coord(pb.y, sc.origin[1], sc.cell, sc.dims[1]);
+    const int32_t cz = cell_coord(pb.z, sc.origin[2], sc.cell, sc.dims[2]);
+    const int32_t x0 = max(cx - 1, 0), x1 = min(cx + 1, sc.dims[0] - 1);
+    float ws = 0.0f;
+    for (int32_t dz = -1; dz <= 1; ++dz) {
+        const int32_t z = cz + dz;
+        if (z < 0 || z >= sc.dims[2]) continue;
+        for (int32_t dy = -1; dy <= 1; ++dy) {
+            const int32_t y = cy + dy;
+            if (y < 0 || y >= sc.dims[1]) continue;
+            const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
+            const uint32_t jb = P.bcell_start[row + x0], je = P.bcell_start[row + x1 + 1];
+            for (uint32_t k = jb; k < je; ++k) {
+                if ((int64_t)k == b) continue;
+                float dx, dy2, dz2;
+                const float d2 = pred_d2(pb, P.bpos_s[k], dx, dy2, dz2);
+                if (!(d2 < sc.h2)) continue;
+                ws += spline_w(sqrtf(d2) * sc.inv_h);
+            }
+        }
+    }
+    reinterpret_cast<float *>(P.bpos_s + b)[3] = sc.rho0 / (sc.sigma * (1.0f + ws));
+}
+
+__device__ double block_sum_d(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kBlock / 32; ++k) t += sh[k];
+    return t;
+}
+
+// Force and torque of the fluid on each body of the scene for the step just solved.
+__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int max_bodies)
+{
+    __shared__ double sh[kBlock / 32];
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    const int32_t scene = P.fblk_scene[blockIdx.x];
+    const SceneDev &sc = P.scenes[scene];
+    SceneState &st = P.st[scene];
+    if (sc.nbody == 0) return;
+    int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
+    const bool valid = local < sc.nf;
+    const int64_t i = sc.f_off + local;
+    int nb = 0;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    float kt = 0.0f;
+    if (valid) {
+        nb = P.nnb[i];
+        pi = P.pos_s[i];
+        kt = (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
+    }
+    // most blocks have no particle next to any boundary: write zero partials and skip
+    const bool any = __syncthreads_or(nb > 0) != 0;
+    for (int k = 0; k < sc.nbody; ++k) {
+        double f[6] = {0, 0, 0, 0, 0, 0};
+        if (any) {
+            const BodyDev &B = P.bodies[sc.body_off + k];
+            for (int t = 0; t < nb; ++t) {
+                const int32_t b = P.bnbr[(int64_t)t * P.NF + i];
+                if (P.bbody_s[b] != k) continue;
+                const float4 pb = P.bpos_s[b];
+                const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
+                const float g = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                const double s = (double)sc.m * (double)pb.w * (double)kt * (double)g;
+                const double Fx = s * dx, Fy = s * dy, Fz = s * dz;
+                const double rx = (double)pb.x - B.com[0], ry = (double)pb.y - B.com[1], rz = (double)pb.z - B.com[2];
+                f[0] += Fx; f[1] += Fy; f[2] += Fz;
+                f[3] += ry * Fz - rz * Fy;
+                f[4] += rz * Fx - rx * Fz;
+                f[5] += rx * Fy - ry * Fx;
+            }
+        }
+        for (int a = 0; a < 6; ++a) {
+            double t = any ? block_sum_d(f[a], sh) : 0.0;
+            if (threadIdx.x == 0) P.body_partial[((int64_t)blockIdx.x * max_bodies + k) * 6 + a] = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        uint32_t prev = atomicAdd(&st.counter, 1u);
+        s_last = (prev == (uint32_t)sc.fblk_count - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const volatile double *part = P.body_partial;
+    for (int k = 0; k < sc.nbody; ++k) {
+        for (int a = 0; a < 6; ++a) {
+            double t = 0.0;
+            for (int q = threadIdx.x; q < sc.fblk_count; q += kBlock)
+                t += part[((int64_t)(sc.fblk_first + q) * max_bodies + k) * 6 + a];
+            double tot = block_sum_d(t, sh);
+            if (threadIdx.x == 0) {
+                BodyDev &B = P.bodies[sc.body_off + k];
+                if (a < 3) B.force[a] = tot;
+                else B.torque[a - 3] = tot;
+            }
+        }
+    }
+    if (threadIdx.x == 0) st.counter = 0;
+}
+
+}  // namespace
+
+void launch_boundary_update(const Ptrs &P, cudaStream_t s)
+{
+    if (P.nbblk) k_boundary_update<<<P.nbblk, kBlock, 0, s>>>(P);
+}
+void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s)
+{
+    if (P.nbblk) k_boundary_psi<<<P.nbblk, kBlock, 0, s>>>(P, only_moving);
+}
+void launch_body_force(const Ptrs &P, int max_bodies, cudaStream_t s)
+{
+    if (P.nfblk) k_body_force<<<P.nfblk, kBlock, 0, s>>>(P, max_bodies);
+}
+
+}  // namespace sph

@@ -1,0 +1,96 @@
+"""GPU runtime behaviour: status codes, checkpoint/resume, graph vs eager replay, batched
+scenes vs single scenes, launch counting."""
+import numpy as np
+import pytest
+
+from paper_2403_11156_gb300 import scenes, sph
+
+from gpu_util import gpu_ctx
+
+pytestmark = pytest.mark.gpu
+DT = 4e-4
+
+
+def _small(seed=7, **kw):
+    return scenes.dam_break_small(seed=seed, n=(9, 11, 13), box=0.4, **kw)
+
+
+def test_noconverge_reported_and_state_advances():
+    d = _small(max_iter_density=1, min_iter_density=1, eta_density=1e-12)
+    g = gpu_ctx(d)
+    x0 = g.sph_read_state()[0]
+    g.sph_step(DT)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_ENOCONVERGE
+    st = g.sph_get_stats()
+    assert st["dens_iters"] == 1 and st["flags"] & 2
+    assert not np.array_equal(g.sph_read_state()[0], x0)
+    g.sph_step(DT)                                     # context still usable
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK   # already reported
+
+
+def test_overflow_reported():
+    g = gpu_ctx(_small(max_fluid_neighbors=8))
+    g.sph_step(DT)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_EOVERFLOW
+    assert g.sph_get_stats()["max_fluid_nbrs"] > 8
+
+
+def test_checkpoint_resume_bit_exact():
+    d = _small()
+    a = gpu_ctx(d)
+    a.sph_steps(6, DT)
+    x, v, _, _ = a.sph_read_state()
+    kp = a.sph_read_field(sph.FIELD_KAPPA_PREV)
+    kvp = a.sph_read_field(sph.FIELD_KAPPA_V_PREV)
+    b = gpu_ctx(d)
+    b.sph_write_state(0, x, v, kp, kvp)
+    for ctx in (a, b):
+        ctx.sph_steps(3, DT)
+    xa, va, ra, pa = a.sph_read_state()
+    xb, vb, rb, pb = b.sph_read_state()
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(pa, pb)
+
+
+def test_graph_and_eager_identical():
+    d = _small(cfl=0.4, dt_max=1e-3)
+    a = gpu_ctx(d)
+    b = gpu_ctx(d)
+    b.sph_set_mode(graph=False, timing=True)
+    for ctx in (a, b):
+        ctx.sph_steps(8, 0.0)
+    for u, w in zip(a.sph_read_state(), b.sph_read_state()):
+        np.testing.assert_array_equal(u, w)
+    assert a.sph_get_stats()["total_dens_iters"] == b.sph_get_stats()["total_dens_iters"]
+    assert a.sph_launch_count() == b.sph_launch_count()
+    kt = b.sph_kernel_times()
+    assert kt["density_alpha"][0] == 8 and kt["advect"][0] == 8
+
+
+def test_batch_equals_single():
+    ds = [_small(seed=3), scenes.dam_break_small(seed=4, n=(17, 5, 9), box=0.5, warm_start=0),
+          _small(seed=5, viscosity_mode=2, xsph_c=0.1)]
+    batch = gpu_ctx(ds)
+    batch.sph_steps(6, DT)
+    for k, d in enumerate(ds):
+        single = gpu_ctx(d)
+        single.sph_steps(6, DT)
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w)
+        assert batch.sph_get_stats(k)["total_dens_iters"] == single.sph_get_stats()["total_dens_iters"]
+
+
+def test_read_state_device_matches_host():
+    import torch
+    d = _small()
+    g = gpu_ctx(d)
+    g.sph_steps(2, DT)
+    n = len(d["fluid_x"])
+    x = torch.empty((n, 3), device="cuda")
+    p = torch.empty(n, device="cuda")
+    g.sph_read_state_device(0, x=x, pressure=p)
+    hx, _, _, hp = g.sph_read_state()
+    np.testing.assert_array_equal(x.cpu().numpy(), hx)
+    np.testing.assert_array_equal(p.cpu().numpy(), hp)
