@@ -227,6 +227,29 @@ sph_status sph_kernel_times(sph_ctx *ctx, sph_kernel_time *out, int32_t cap, int
 /* Kernel launches enqueued since creation (counted on the device for graph replays). */
 sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
 
+/* Grid order of a point set with no memory allocation (this library's addition; the paper
+ * has no counterpart).  For callers that cannot let a library allocate: code enqueueing
+ * work while another component captures a CUDA graph, applications that own the GPU's
+ * memory budget, real-time loops.  Runs the per-step counting sort of the neighbour search
+ * (same float cell-key contract and (cell key, index) order as sph_step) on
+ *   x     device float [n][3] positions,
+ *   domain_min, domain_max  host float[3], cell_size > 0 (grid as in sph_scene_desc),
+ * writing
+ *   order device int32 [n]: point indices in (cell key, index) order,
+ *   keys  device uint32 [n] or NULL: each point's cell key (input order),
+ * on stream (a cudaStream_t, NULL = legacy default).  Returns after enqueueing.
+ * Its scratch is one static device array of about 12 MB that every GPU loading this
+ * library holds until the process exits, shared by all calls: n above
+ * SPH_NOALLOC_MAX_POINTS or a grid above SPH_NOALLOC_MAX_CELLS cells returns SPH_EINVAL,
+ * and calls whose work overlaps on the GPU (different streams, or host threads) race on
+ * that array.  The first call on a device looks up the array's device address (with that
+ * device current) and should come before any stream capture.  Calls no allocator. */
+#define SPH_NOALLOC_MAX_POINTS 262144
+#define SPH_NOALLOC_MAX_CELLS 1048576
+sph_status sph_grid_order_noalloc(const float *x, int64_t n, const float *domain_min,
+                                  const float *domain_max, float cell_size, int32_t *order,
+                                  uint32_t *keys, void *stream);
+
 const char *sph_status_string(sph_status s);
 
 /* Message of the last failing call on ctx (never NULL). */

@@ -128,9 +128,11 @@ def load():
     L.sph_last_error.restype = C.c_char_p
     L.sph_last_error.argtypes = [vp]
     L.sph_destroy.argtypes = [vp]
+    L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
-                 "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count"):
+                 "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
+                 "sph_grid_order_noalloc"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -340,3 +342,19 @@ class Context:
         n = C.c_int64()
         _check(self.ctx, load().sph_launch_count(self.ctx, C.byref(n)))
         return n.value
+
+
+NOALLOC_MAX_POINTS = 262144
+NOALLOC_MAX_CELLS = 1048576
+
+
+def sph_grid_order_noalloc(x, n, domain_min, domain_max, cell_size, order, keys=None, stream=None):
+    """Marshal sph_grid_order_noalloc: x, order, keys are device pointers (ints or tensors
+    with data_ptr()); domain bounds are 3-sequences; returns the status code."""
+    def ptr(t):
+        return None if t is None else (t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    lo = (C.c_float * 3)(*domain_min)
+    hi = (C.c_float * 3)(*domain_max)
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return load().sph_grid_order_noalloc(ptr(x), int(n), lo, hi, float(cell_size), ptr(order),
+                                         ptr(keys), st)
