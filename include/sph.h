@@ -224,6 +224,27 @@ typedef struct sph_kernel_time {
 sph_status sph_kernel_times(sph_ctx *ctx, sph_kernel_time *out, int32_t cap, int32_t *n,
                             int32_t reset);
 
+/* Learned warm start (this library's addition; the paper has no learned component).
+ * A per-particle network y = W3 gelu(W2 gelu(W1 f + b1) + b2) + b3 (hidden width 64,
+ * exact-erf GELU, BF16 tensor-core layers with FP32 accumulation) maps the standardised
+ * features f = (rho/rho0 - 1, dt Drho/Dt(v*)/rho0, (n_f + n_b)/33, kappa_prev/(9.81 h))
+ * to the standardised converged density stiffness; the warm start of the constant-
+ * density solve is kappa0 = max((y std_y + mean_y) 9.81 h, 0) where the fluid compresses.
+ * Parameter block, float [SPH_MLP_PARAMS]: W1[64][4], b1[64], W2[64][64], b2[64],
+ * W3[64], b3, feature mean[4], feature std[4], label mean, label std. */
+#define SPH_MLP_PARAMS 4555
+#define SPH_MLP_WEIGHTS 4545
+
+/* Load the network used by scenes with warm_start = SPH_WARM_LEARNED (host array,
+ * copied).  Until it is called those scenes start the density solve from zero. */
+sph_status sph_set_mlp(sph_ctx *ctx, const float *params, int64_t n);
+
+/* Network forward on device arrays: params [SPH_MLP_PARAMS], standardised features
+ * [n][4] -> y [n] (standardised output).  *error (device int32) is set to 1 if a
+ * tensor-core wait gave up.  Enqueued on stream; returns after enqueueing. */
+sph_status sph_mlp_forward(const float *params, const float *features, int64_t n, float *y,
+                           int32_t *error, void *stream);
+
 /* Kernel launches enqueued since creation (counted on the device for graph replays). */
 sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
 

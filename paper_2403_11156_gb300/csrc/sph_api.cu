@@ -383,9 +383,9 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     run(c, s, "sort_rank_gather", [&] { launch_rank_gather(P, SORT_FLUID, s); });
     run(c, s, "density_alpha", [&] { launch_density_alpha(P, s); });
 
-    auto loop = [&](int solver) -> sph_status {
-        const char *na = solver == 0 ? "div_pass_a" : "dens_pass_a";
-        const char *nb = solver == 0 ? "div_pass_b" : "dens_pass_b";
+    // A device-controlled loop: in capture mode a conditional while node whose body is
+    // captured on the second stream; in eager mode the host reads the loop flag.
+    auto device_loop = [&](auto &&body) -> sph_status {
         if (capture) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t g;
@@ -401,24 +401,29 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
             np.conditional.size = 1;
             cudaGraphNode_t node;
             CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
-            cudaGraph_t body = np.conditional.phGraph_out[0];
+            cudaGraph_t bodyg = np.conditional.phGraph_out[0];
             CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-            CK(cudaStreamBeginCaptureToGraph(c->cap1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-            launch_pass_a(P, solver, c->cap1);
-            launch_pass_b(P, solver, 0, h, 1, c->cap1);
-            c->host_launches += 2;
+            CK(cudaStreamBeginCaptureToGraph(c->cap1, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            body(c->cap1, h, 1);
             cudaGraph_t out = nullptr;
             CK(cudaStreamEndCapture(c->cap1, &out));
         } else {
             for (int guard = 0; guard < 200000; ++guard) {
-                run(c, s, na, [&] { launch_pass_a(P, solver, s); });
-                run(c, s, nb, [&] { launch_pass_b(P, solver, 0, 0, 0, s); });
+                body(s, (cudaGraphConditionalHandle)0, 0);
                 CK(cudaMemcpyAsync(c->h_flag, &P.ctl->loop_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 if (*c->h_flag == 0) break;
             }
         }
         return SPH_OK;
+    };
+    auto loop = [&](int solver) -> sph_status {
+        const char *na = solver == 0 ? "div_pass_a" : "dens_pass_a";
+        const char *nb = solver == 0 ? "div_pass_b" : "dens_pass_b";
+        return device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
+            run(c, q, na, [&] { launch_pass_a(P, solver, q); });
+            run(c, q, nb, [&] { launch_pass_b(P, solver, 0, h, use, q); });
+        });
     };
 
     sph_status st;
@@ -427,12 +432,25 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         if ((st = loop(0)) != SPH_OK) return st;
     }
     run(c, s, "nonpressure", [&] { launch_nonpressure(P, s); });
+    if (c->any_implicit) {
+        run(c, s, "cg_init", [&] { launch_cg_init(P, s); });
+        st = device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
+            run(c, q, "cg_ap", [&] { launch_cg_ap(P, q); });
+            run(c, q, "cg_xr", [&] { launch_cg_xr(P, q); });
+            run(c, q, "cg_p", [&] { launch_cg_p(P, h, use, q); });
+        });
+        if (st != SPH_OK) return st;
+    }
     if (c->any_warm) {
         run(c, s, "warm_density", [&] { launch_warm_density(P, s); });
+        if (c->any_learned) run(c, s, "mlp_warm", [&] { launch_mlp_warm(P, s); });
         run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, 0, 0, s); });
     }
     if ((st = loop(1)) != SPH_OK) return st;
-    if (c->any_bodies) run(c, s, "body_force", [&] { launch_body_force(P, c->max_bodies, s); });
+    if (c->any_bodies) {
+        run(c, s, "body_force", [&] { launch_body_force(P, s); });
+        run(c, s, "body_reduce", [&] { launch_body_reduce(P, s); });
+    }
     run(c, s, "advect", [&] { launch_advect(P, s); });
     run(c, s, "step_end", [&] { launch_step_end(P, s); });
     return SPH_OK;
@@ -616,7 +634,12 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, P.bkey_tmp, NBa) && dalloc(c, P.bslot_tmp, NBa) && dalloc(c, P.bsid_tmp, NBa) &&
           dalloc(c, P.bsrc_tmp, NBa) && dalloc(c, P.bcell_tmp, NBa);
     ok &= dalloc(c, P.partial, std::max(nfblk, 1));
-    ok &= dalloc(c, P.body_partial, (size_t)std::max(nfblk, 1) * std::max(c->max_bodies, 1) * 6);
+    ok &= dalloc(c, P.body_partial, (size_t)std::max(nfblk, 1) * std::max(nbodies, 1) * 6);
+    if (c->any_implicit) {
+        ok &= dalloc(c, P.cg_r, NF) && dalloc(c, P.cg_p, NF) && dalloc(c, P.cg_ap, NF);
+        ok &= dalloc(c, P.cg_dots, 2 * (size_t)std::max(nfblk, 1));
+    }
+    ok &= dalloc(c, P.mlp_w, SPH_MLP_PARAMS);
     P.scan_tiles = scan_tiles_for(NC);
     ok &= dalloc(c, P.scan_status, std::max(P.scan_tiles, 1));
     if (!ok) return bail(fail(c, SPH_ENOMEM, "device allocation failed"));
@@ -761,6 +784,8 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         sph_status cs = check_async(c);
         if (cs != SPH_OK) return bail(cs);
     }
+    if (c->any_learned && mlp_prepare_kernels() != cudaSuccess)
+        return bail(fail(c, SPH_ECUDA, "network kernel attributes could not be set"));
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(c, SPH_ECUDA, "create: %s", cudaGetErrorString(cudaGetLastError())));
     sph_status gs = build_graph(c);
     if (gs != SPH_OK) return bail(gs);
@@ -1040,6 +1065,23 @@ sph_status sph_kernel_times(sph_ctx *c, sph_kernel_time *out, int32_t cap, int32
     }
     if (n) *n = k;
     if (reset) c->times.clear();
+    return SPH_OK;
+}
+
+sph_status sph_set_mlp(sph_ctx *c, const float *params, int64_t n)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (!params || n != SPH_MLP_PARAMS) return fail(c, SPH_EINVAL, "network parameter block must hold %d floats", SPH_MLP_PARAMS);
+    for (int k = SPH_MLP_WEIGHTS + 4; k < SPH_MLP_WEIGHTS + 8; ++k)
+        if (!(params[k] > 0.0f)) return fail(c, SPH_EINVAL, "feature std must be > 0");
+    if (!(params[SPH_MLP_PARAMS - 1] > 0.0f)) return fail(c, SPH_EINVAL, "label std must be > 0");
+    for (int64_t k = 0; k < n; ++k)
+        if (!std::isfinite(params[k])) return fail(c, SPH_EINVAL, "non-finite network parameter");
+    CK(cudaMemcpyAsync(c->P.mlp_w, params, sizeof(float) * SPH_MLP_PARAMS, cudaMemcpyHostToDevice, c->stream));
+    const int32_t one = 1;
+    CK(cudaMemcpyAsync(&c->P.ctl->have_mlp, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
 

@@ -125,6 +125,44 @@ __global__ void k_step_begin(Ptrs P)
     st.maxv2 = 0.0f;
 }
 
+// Visit the entries [0, n) of particle i's k-major list in batches of U: the U index loads
+// of a batch are issued together, then the U visits, whose gathers the compiler can then
+// keep in flight together (the visits only accumulate in registers).  The visiting order,
+// and so the floating-point summation order, is the list order.
+template <int U, bool NC = true, typename F>
+__device__ __forceinline__ void for_list(const int32_t *__restrict__ list, int64_t NF, int64_t i, int n,
+                                         F &&visit)
+{
+    // NC: the list is read-only for the whole kernel (read-only data path); otherwise
+    // plain loads, for a list this thread has just written
+    auto ld = [&](int k) { return NC ? __ldg(list + (int64_t)k * NF + i) : list[(int64_t)k * NF + i]; };
+    int k = 0;
+    for (; k + U <= n; k += U) {
+        int32_t j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) j[u] = ld(k + u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) visit(j[u]);
+    }
+    for (; k < n; ++k) visit(ld(k));
+}
+
+// Visit the contiguous candidate range [jb, je) of a grid row in batches of U: the U
+// position loads of a batch are issued before any visit, in index order.
+template <int U, typename F>
+__device__ __forceinline__ void for_range(const float4 *__restrict__ pos, uint32_t jb, uint32_t je, F &&visit)
+{
+    uint32_t j = jb;
+    for (; j + U <= je; j += U) {
+        float4 p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) p[u] = __ldg(pos + j + u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) visit(j + u, p[u]);
+    }
+    for (; j < je; ++j) visit(j, __ldg(pos + j));
+}
+
 // ------------------------------------------------------------------------------------
 // Density (Eq. density + Sec. 3.5 boundary term), DFSPH alpha, neighbour lists, and the
 // gate of the divergence warm start (D rho/Dt with the velocities at step start).
@@ -143,8 +181,12 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         const int32_t cz = cell_coord(pi.z, sc.origin[2], sc.cell, sc.dims[2]);
         const int32_t x0 = max(cx - 1, 0), x1 = min(cx + 1, sc.dims[0] - 1);
         const float h2 = sc.h2;
-        const bool gate = sc.warm != 0 && sc.div_on;
-        float w_sum = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, s2 = 0.0f, div_f = 0.0f;
+        const int cap_f = sc.cap_f, cap_b = sc.cap_b;
+        int32_t *__restrict__ nbr = P.nbr;
+        int32_t *__restrict__ bnbr = P.bnbr;
+        // phase 1: the float predicate over the 27-cell stencil (9 contiguous index
+        // ranges) only records neighbours; keeping the expensive per-pair work out of this
+        // loop keeps the warp converged while most candidates are rejected
         for (int32_t dz = -1; dz <= 1; ++dz) {
             const int32_t z = cz + dz;
             if (z < 0 || z >= sc.dims[2]) continue;
@@ -153,61 +195,67 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
                 if (y < 0 || y >= sc.dims[1]) continue;
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
                 const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
-                for (uint32_t j = jb; j < je; ++j) {
-                    if ((int64_t)j == i) continue;
-                    const float4 pj = P.pos_s[j];
+                for_range<2>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
                     float dx, dy2, dz2;
                     const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-                    if (!(d2 < h2)) continue;
-                    if (nn_f < sc.cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
-                    ++nn_f;
-                    const float r = sqrtf(d2);
-                    w_sum += spline_w(r * sc.inv_h);
-                    const float f = grad_factor(sc, d2);
-                    const float gx = f * dx, gy = f * dy2, gz = f * dz2;
-                    s1x += gx; s1y += gy; s1z += gz;
-                    s2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, s2)));
-                    if (gate) {
-                        const float4 vj = P.vel_s[j];
-                        div_f += (vi.x - vj.x) * gx + (vi.y - vj.y) * gy + (vi.z - vj.z) * gz;
+                    if (d2 < h2 && (int64_t)j != i) {
+                        if (nn_f < cap_f) nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
+                        ++nn_f;
                     }
+                });
+                if (sc.nb > 0) {
+                    const uint32_t bb = P.bcell_start[row + x0], be = P.bcell_start[row + x1 + 1];
+                    for_range<1>(P.bpos_s, bb, be, [&](uint32_t b, float4 pb) {
+                        float dx, dy2, dz2;
+                        const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
+                        if (d2 < h2) {
+                            if (nn_b < cap_b) bnbr[(int64_t)nn_b * NF + i] = (int32_t)b;
+                            ++nn_b;
+                        }
+                    });
                 }
             }
         }
+        const int nf = min(nn_f, cap_f), nb = min(nn_b, cap_b);
+        // phase 2: density, alpha and the warm-start gate over the recorded lists (the
+        // same pairs in the same order as the stencil walk)
+        const bool gate = sc.warm != 0 && sc.div_on;
+        float w_sum = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, s2 = 0.0f, div_f = 0.0f;
+        for_list<2, false>(nbr, NF, i, nf, [&](int32_t j) {
+            const float4 pj = __ldg(P.pos_s + j);
+            float dx, dy2, dz2;
+            const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
+            w_sum += spline_w(sqrtf(d2) * sc.inv_h);
+            const float f = grad_factor(sc, d2);
+            const float gx = f * dx, gy = f * dy2, gz = f * dz2;
+            s1x += gx; s1y += gy; s1z += gz;
+            s2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, s2)));
+            if (gate) {
+                const float4 vj = __ldg(P.vel_s + j);
+                div_f += (vi.x - vj.x) * gx + (vi.y - vj.y) * gy + (vi.z - vj.z) * gz;
+            }
+        });
         float rho = sc.m * sc.sigma * (1.0f + w_sum);
         s1x *= sc.m; s1y *= sc.m; s1z *= sc.m;
         s2 *= sc.m * sc.m;
         float div = sc.m * div_f;
-        if (sc.nb > 0) {
+        if (nb > 0) {
             float wb = 0.0f, divb = 0.0f;
-            for (int32_t dz = -1; dz <= 1; ++dz) {
-                const int32_t z = cz + dz;
-                if (z < 0 || z >= sc.dims[2]) continue;
-                for (int32_t dy = -1; dy <= 1; ++dy) {
-                    const int32_t y = cy + dy;
-                    if (y < 0 || y >= sc.dims[1]) continue;
-                    const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
-                    const uint32_t jb = P.bcell_start[row + x0], je = P.bcell_start[row + x1 + 1];
-                    for (uint32_t b = jb; b < je; ++b) {
-                        const float4 pb = P.bpos_s[b];
-                        float dx, dy2, dz2;
-                        const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
-                        if (!(d2 < h2)) continue;
-                        if (nn_b < sc.cap_b) P.bnbr[(int64_t)nn_b * NF + i] = (int32_t)b;
-                        ++nn_b;
-                        const float r = sqrtf(d2);
-                        const float psi = pb.w;
-                        wb += psi * spline_w(r * sc.inv_h);
-                        const float f = psi * grad_factor(sc, d2);
-                        const float gx = f * dx, gy = f * dy2, gz = f * dz2;
-                        s1x += gx; s1y += gy; s1z += gz;
-                        if (gate) {
-                            float4 vb = sc.has_moving ? P.bvel_s[b] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            divb += (vi.x - vb.x) * gx + (vi.y - vb.y) * gy + (vi.z - vb.z) * gz;
-                        }
-                    }
+            const bool moving = sc.has_moving != 0;
+            for_list<1, false>(bnbr, NF, i, nb, [&](int32_t b) {
+                const float4 pb = __ldg(P.bpos_s + b);
+                float dx, dy2, dz2;
+                const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
+                const float psi = pb.w;
+                wb += psi * spline_w(sqrtf(d2) * sc.inv_h);
+                const float f = psi * grad_factor(sc, d2);
+                const float gx = f * dx, gy = f * dy2, gz = f * dz2;
+                s1x += gx; s1y += gy; s1z += gz;
+                if (gate) {
+                    float4 vb = moving ? __ldg(P.bvel_s + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    divb += (vi.x - vb.x) * gx + (vi.y - vb.y) * gy + (vi.z - vb.z) * gz;
                 }
-            }
+            });
             rho += sc.sigma * wb;
             div += divb;
         }
@@ -215,8 +263,8 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         const float alpha = den > sc.eps_alpha ? rho / den : 0.0f;
         P.alpha[i] = alpha;
         set_w(P.vel_s, i, rho);
-        P.nnf[i] = min(nn_f, sc.cap_f);
-        P.nnb[i] = min(nn_b, sc.cap_b);
+        P.nnf[i] = nf;
+        P.nnb[i] = nb;
         float kv0 = 0.0f;
         if (gate && div > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
         P.kvsum[i] = kv0;
@@ -233,35 +281,34 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
 // ------------------------------------------------------------------------------------
 // D rho_i/Dt = sum_j m (v_i - v_j).grad W_ij + sum_b Psi_b (v_i - v_b).grad W_ib
 // (SPH divergence of Sec. 3.2 in the continuity equation, boundary per Sec. 3.5).
+constexpr int kBatch = 4;
+
 __device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi,
                                          float4 vi, const float4 *__restrict__ V)
 {
     const int64_t NF = P.NF;
-    const int nn = P.nnf[i];
     float acc = 0.0f;
-    for (int k = 0; k < nn; ++k) {
-        const int32_t j = P.nbr[(int64_t)k * NF + i];
-        const float4 pj = P.pos_s[j];
-        const float4 vj = V[j];
+    for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+        const float4 pj = __ldg(P.pos_s + j);
+        const float4 vj = __ldg(V + j);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         acc = fmaf(f, (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz, acc);
-    }
+    });
     acc *= sc.m;
-    const int nb = P.nnb[i];
     float accb = 0.0f;
-    for (int k = 0; k < nb; ++k) {
-        const int32_t b = P.bnbr[(int64_t)k * NF + i];
-        const float4 pb = P.bpos_s[b];
+    const bool moving = sc.has_moving != 0;
+    for_list<4>(P.bnbr, NF, i, P.nnb[i], [&](int32_t b) {
+        const float4 pb = __ldg(P.bpos_s + b);
         const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
         const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         float ux = vi.x, uy = vi.y, uz = vi.z;
-        if (sc.has_moving) {
-            const float4 vb = P.bvel_s[b];
+        if (moving) {
+            const float4 vb = __ldg(P.bvel_s + b);
             ux -= vb.x; uy -= vb.y; uz -= vb.z;
         }
         accb = fmaf(f, ux * dx + uy * dy + uz * dz, accb);
-    }
+    });
     return acc + accb;
 }
 
@@ -345,25 +392,21 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
         const float4 pi = P.pos_s[i];
         const float ki = pi.w;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        const int nn = P.nnf[i];
-        for (int k = 0; k < nn; ++k) {
-            const int32_t j = P.nbr[(int64_t)k * NF + i];
-            const float4 pj = P.pos_s[j];
+        for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+            const float4 pj = __ldg(P.pos_s + j);
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
             ax = fmaf(f, dx, ax); ay = fmaf(f, dy, ay); az = fmaf(f, dz, az);
-        }
+        });
         ax *= sc.m; ay *= sc.m; az *= sc.m;
         if (ki != 0.0f) {
-            const int nb = P.nnb[i];
             float bx = 0.0f, by = 0.0f, bz = 0.0f;
-            for (int k = 0; k < nb; ++k) {
-                const int32_t b = P.bnbr[(int64_t)k * NF + i];
-                const float4 pb = P.bpos_s[b];
+            for_list<4>(P.bnbr, NF, i, P.nnb[i], [&](int32_t b) {
+                const float4 pb = __ldg(P.bpos_s + b);
                 const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
                 const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 bx = fmaf(f, dx, bx); by = fmaf(f, dy, by); bz = fmaf(f, dz, bz);
-            }
+            });
             ax = fmaf(ki, bx, ax); ay = fmaf(ki, by, ay); az = fmaf(ki, bz, az);
         }
         const float dt = st.dt;
@@ -426,16 +469,15 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
     float ax = sc.g[0], ay = sc.g[1], az = sc.g[2];
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     if (sc.visc_mode == 1 || sc.visc_mode == 2) {
-        const int nn = P.nnf[i];
         const float reg = 0.01f * sc.h2;
-        for (int k = 0; k < nn; ++k) {
-            const int32_t j = P.nbr[(int64_t)k * NF + i];
-            const float4 pj = P.pos_s[j];
-            const float4 vj = P.vel_s[j];
+        const bool lap = sc.visc_mode == 1;
+        for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+            const float4 pj = __ldg(P.pos_s + j);
+            const float4 vj = __ldg(P.vel_s + j);
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (sc.visc_mode == 1) {
+            if (lap) {
                 const float f = grad_factor(sc, r2);
                 const float s = f * (ux * dx + uy * dy + uz * dz) / ((r2 + reg) * vj.w);
                 sx = fmaf(s, dx, sx); sy = fmaf(s, dy, sy); sz = fmaf(s, dz, sz);
@@ -443,7 +485,7 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
                 const float w = spline_w(sqrtf(r2) * sc.inv_h) / vj.w;
                 sx = fmaf(-w, ux, sx); sy = fmaf(-w, uy, sy); sz = fmaf(-w, uz, sz);
             }
-        }
+        });
     }
     float4 v = vi;
     if (sc.visc_mode == 1) {
@@ -483,7 +525,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     float k0 = 0.0f;
     if (sc.warm == 1) {
         if (dev > 0.0f) k0 = 0.5f * P.kprev_s[i] / (dt * dt);
-    } else if (P.have_mlp) {
+    } else if (P.ctl->have_mlp) {
         const float kref = 9.81f * sc.h;
         float4 f;
         f.x = rho / sc.rho0 - 1.0f;

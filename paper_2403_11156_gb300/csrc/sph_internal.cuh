@@ -61,7 +61,9 @@ struct SceneState {
     int32_t max_nn_f, max_nn_b;
     int32_t cg_it;
     float cg_res;
+    int32_t cg_active;
     int32_t clamps;
+    double cg_rr, cg_bb, cg_alpha, cg_beta;
     int64_t steps;
     int64_t total_it[2];
 };
@@ -90,6 +92,7 @@ struct Control {
     int32_t scan_done;
     uint32_t scan_epoch;
     int32_t error;                    // bounded-wait failures
+    int32_t have_mlp;                 // warm-start network loaded
 };
 
 struct Ptrs {
@@ -123,16 +126,14 @@ struct Ptrs {
     uint32_t *bkey_tmp, *bslot_tmp, *bsid_tmp, *bsrc_tmp, *bcell_tmp;
     // reductions
     double *partial;                  // [nfblk]
-    double *body_partial;             // [nfblk][6] per body pass
+    double *body_partial;             // [body][6][nfblk] per-block force/torque partials
     uint64_t *scan_status;            // [tiles]
     int32_t scan_tiles;
     // implicit viscosity CG
     float4 *cg_r, *cg_p, *cg_ap;
     double *cg_dots;                  // per-block partials [nfblk][2]
-    double *cg_scal;                  // per-scene scalars [S][4]: rr, pAp, bb, alpha...
     // network
-    const float *mlp_w;               // device weights (float master copy)
-    int32_t have_mlp;
+    float *mlp_w;                     // device parameter block (float)
 };
 
 // ------------------------------------------------------------------ grid (sph_grid.cu)
@@ -176,9 +177,20 @@ void launch_advect(const Ptrs &P, cudaStream_t s);
 void launch_step_end(const Ptrs &P, cudaStream_t s);
 void launch_set_dt(const Ptrs &P, float dt, cudaStream_t s);
 
+// ------------------------------------------------------------------ network (sph_mlp.cu)
+void launch_mlp_warm(const Ptrs &P, cudaStream_t s);
+cudaError_t mlp_prepare_kernels();
+
+// ------------------------------------------------------------------ implicit viscosity (sph_visc.cu)
+void launch_cg_init(const Ptrs &P, cudaStream_t s);
+void launch_cg_ap(const Ptrs &P, cudaStream_t s);
+void launch_cg_xr(const Ptrs &P, cudaStream_t s);
+void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+
 // ------------------------------------------------------------------ rigid (sph_rigid.cu)
 void launch_boundary_update(const Ptrs &P, cudaStream_t s);
 void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);
-void launch_body_force(const Ptrs &P, int max_bodies, cudaStream_t s);
+void launch_body_force(const Ptrs &P, cudaStream_t s);
+void launch_body_reduce(const Ptrs &P, cudaStream_t s);
 
 }  // namespace sph

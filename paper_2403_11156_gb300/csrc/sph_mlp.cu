@@ -1,0 +1,247 @@
+// sph_mlp.cu -- learned warm start of the constant-density solve (this library's
+// addition; the paper has no learned component): a per-particle network
+//   y = W3 gelu(W2 gelu(W1 f + b1) + b2) + b3,   f in R^4, hidden 64, exact-erf GELU,
+// on standardised features f = (raw - mean) / std; the prediction kappa0 =
+// max((y std_y + mean_y) 9.81 h, 0) applies where the fluid compresses.  Both hidden
+// layers run on the tcgen05 tensor cores (BF16 operands, FP32 accumulation in tensor
+// memory) for a tile of 128 particles per CTA; the 64-wide output dot product runs on the
+// CUDA cores while the second layer's accumulators are read back.
+//
+// Parameter block (float, length kMlpParams): W1[64][4], b1[64], W2[64][64], b2[64],
+// W3[64], b3, feature mean[4], feature std[4], label mean, label std.
+#include <cuda_bf16.h>
+
+#include "sph.h"
+#include "sph_internal.cuh"
+#include "sph_tc.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kH = 64;
+constexpr int kF = 4;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kH * kF;
+constexpr int kOffW2 = kOffB1 + kH;
+constexpr int kOffB2 = kOffW2 + kH * kH;
+constexpr int kOffW3 = kOffB2 + kH;
+constexpr int kOffB3 = kOffW3 + kH;
+constexpr int kNW = kOffB3 + 1;
+constexpr int kOffMuF = kNW;
+constexpr int kOffSdF = kOffMuF + kF;
+constexpr int kOffMuY = kOffSdF + kF;
+constexpr int kOffSdY = kOffMuY + 1;
+constexpr int kMlpParams = kOffSdY + 1;
+static_assert(kMlpParams == SPH_MLP_PARAMS, "parameter block layout");
+
+// shared-memory map of one CTA (bytes)
+constexpr uint32_t kSmA1 = 0;          // 128 x 16 bf16
+constexpr uint32_t kSmB1 = 4096;       // 64 x 16 bf16
+constexpr uint32_t kSmA2 = 8192;       // 128 x 64 bf16
+constexpr uint32_t kSmB2 = 24576;      // 64 x 64 bf16
+constexpr uint32_t kSmVec = 32768;     // b1, b2, w3 (float[64] each)
+constexpr uint32_t kSmBar = 33536;     // mbarrier
+constexpr uint32_t kSmTmem = 33544;    // tensor-memory address
+constexpr uint32_t kSmUsed = 33600;
+// requested dynamic shared memory: caps residency at 3 CTAs per SM, so 3 x 128
+// tensor-memory columns never exceed the SM's 512
+constexpr uint32_t kSmRequest = 72 * 1024;
+constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kWaitLimit = 1u << 20;
+
+__device__ __forceinline__ void count_launch(Control *ctl)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Store 8 bf16 (one core-matrix row) at tile element (r, k0) of an R x K K-major tile.
+__device__ __forceinline__ void store8(unsigned char *tile, uint32_t r, uint32_t k0, uint32_t K, const float *v)
+{
+    uint4 q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(tile + tc::tile_offset(r, k0, K)) = q;
+}
+
+// The network for the CTA's 128 rows; thread t owns row t.  f: standardised features.
+// Returns the standardised output y.  *ok is cleared if a tensor-core wait gave up.
+__device__ float mlp_tile(const float *__restrict__ w, const float f[4], unsigned char *sm, bool *ok)
+{
+    const int t = threadIdx.x, warp = t >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kSmTmem);
+    float *b1 = reinterpret_cast<float *>(sm + kSmVec);
+    float *b2 = b1 + kH;
+    float *w3 = b2 + kH;
+    if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+    if (t == 0) tc::mbar_init(bar, 1);
+    // layer-1 operand A: row t = (f0..f3, 0 x 12); B1 row n = W1[n][0..3], 0 x 12
+    {
+        float v[8] = {f[0], f[1], f[2], f[3], 0.f, 0.f, 0.f, 0.f};
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        store8(sm + kSmA1, t, 0, 16, v);
+        store8(sm + kSmA1, t, 8, 16, z);
+        if (t < kH) {
+            float u[8] = {w[kOffW1 + t * kF + 0], w[kOffW1 + t * kF + 1], w[kOffW1 + t * kF + 2],
+                          w[kOffW1 + t * kF + 3], 0.f, 0.f, 0.f, 0.f};
+            store8(sm + kSmB1, t, 0, 16, u);
+            store8(sm + kSmB1, t, 8, 16, z);
+            b1[t] = w[kOffB1 + t];
+            b2[t] = w[kOffB2 + t];
+            w3[t] = w[kOffW3 + t];
+        }
+        for (int idx = t; idx < kH * 8; idx += blockDim.x) {
+            const int n = idx >> 3, kc = (idx & 7) * 8;
+            float u[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) u[q] = w[kOffW2 + n * kH + kc + q];
+            store8(sm + kSmB2, n, kc, kH, u);
+        }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, kH);
+    const uint32_t sbase = tc::smem_addr(sm);
+    if (t == 0) {
+        // D1[128 x 64] = A1[128 x 16] B1[64 x 16]^T: one K = 16 step
+        tc::mma_bf16(tmem, tc::smem_desc(sbase + kSmA1, 128, 256), tc::smem_desc(sbase + kSmB1, 128, 256), idesc, 0);
+        tc::mma_commit(bar);
+    }
+    bool good = tc::mbar_wait_bounded(bar, 0, kWaitLimit);
+    tc::fence_after_sync();
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // hidden layer 1: bias, GELU, BF16 -> layer-2 operand A (row t)
+#pragma unroll
+    for (int c = 0; c < kH / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(tmem + lane_base + c * 16, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = gelu(v[k] + b1[c * 16 + k]);
+        store8(sm + kSmA2, t, c * 16, kH, v);
+        store8(sm + kSmA2, t, c * 16 + 8, kH, v + 8);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+        // D2[128 x 64] = A2[128 x 64] W2^T in four K = 16 steps (two core matrices each)
+#pragma unroll
+        for (int k = 0; k < kH / 16; ++k)
+            tc::mma_bf16(tmem + kH, tc::smem_desc(sbase + kSmA2 + k * 256, 128, 1024),
+                         tc::smem_desc(sbase + kSmB2 + k * 256, 128, 1024), idesc, k > 0 ? 1u : 0u);
+        tc::mma_commit(bar);
+    }
+    good = tc::mbar_wait_bounded(bar, 1, kWaitLimit) && good;
+    tc::fence_after_sync();
+    float y = w[kOffB3];
+#pragma unroll
+    for (int c = 0; c < kH / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(tmem + lane_base + kH + c * 16, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y = fmaf(w3[c * 16 + k], gelu(v[k] + b2[c * 16 + k]), y);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (!good && t == 0) {
+        // an MMA did not report completion: give it one more bounded wait before the
+        // tensor memory is released
+        tc::mbar_wait_bounded(bar, 1, kWaitLimit);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    *ok = good;
+    return y;
+}
+
+// Standalone forward on standardised features [n][4] -> y [n].
+__global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ w, const float4 *__restrict__ feat,
+                                                     int64_t n, float *__restrict__ y, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+        const float4 q = feat[i];
+        f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
+    }
+    bool ok;
+    const float out = mlp_tile(w, f, sm, &ok);
+    if (i < n) y[i] = out;
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+// Learned warm start inside a step: features from k_warm_density (raw), its gate in k0.
+__global__ void __launch_bounds__(128) k_mlp_warm(Ptrs P)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    count_launch(P.ctl);
+    const int32_t s = P.fblk_scene[blockIdx.x];
+    const SceneDev &sc = P.scenes[s];
+    if (sc.warm != 2 || !P.ctl->have_mlp) return;  // uniform per block, before any allocation
+    const int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
+    const bool valid = local < sc.nf;
+    const int64_t i = sc.f_off + local;
+    const float *w = P.mlp_w;
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const float4 q = reinterpret_cast<const float4 *>(P.feat)[i];
+        f[0] = (q.x - w[kOffMuF + 0]) / w[kOffSdF + 0];
+        f[1] = (q.y - w[kOffMuF + 1]) / w[kOffSdF + 1];
+        f[2] = (q.z - w[kOffMuF + 2]) / w[kOffSdF + 2];
+        f[3] = (q.w - w[kOffMuF + 3]) / w[kOffSdF + 3];
+    }
+    bool ok;
+    const float y = mlp_tile(w, f, sm, &ok);
+    if (valid) {
+        const float gate = P.k0[i];
+        const float k0 = gate > 0.0f ? fmaxf((y * w[kOffSdY] + w[kOffMuY]) * 9.81f * sc.h, 0.0f) : 0.0f;
+        P.k0[i] = k0;
+        P.ksum[i] = k0;
+        reinterpret_cast<float *>(P.pos_s + i)[3] = k0 / P.vel_c[i].w;
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(&P.ctl->error, 4);
+}
+
+}  // namespace
+
+void launch_mlp_warm(const Ptrs &P, cudaStream_t s)
+{
+    k_mlp_warm<<<P.nfblk, kBlock, kSmRequest, s>>>(P);
+}
+
+cudaError_t mlp_prepare_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_warm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmRequest);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmRequest);
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" sph_status sph_mlp_forward(const float *params, const float *features, int64_t n, float *y, int32_t *error,
+                                      void *stream)
+{
+    if (n < 0 || (n > 0 && (!params || !features || !y || !error))) return SPH_EINVAL;
+    if (n == 0) return SPH_OK;
+    if (mlp_prepare_kernels() != cudaSuccess) return SPH_ECUDA;
+    const int64_t blocks = (n + 127) / 128;
+    if (blocks > 0x7fffffff) return SPH_EINVAL;
+    k_mlp_forward<<<(unsigned)blocks, 128, kSmRequest, (cudaStream_t)stream>>>(
+        params, reinterpret_cast<const float4 *>(features), n, y, reinterpret_cast<int *>(error));
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;
+}

@@ -109,14 +109,11 @@ __device__ double block_sum_d(double v, double *sh)
 }
 
 // Force and torque of the fluid on each body of the scene for the step just solved.
-__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int max_bodies)
+__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
-    __shared__ int s_last;
     count_launch(P.ctl);
-    const int32_t scene = P.fblk_scene[blockIdx.x];
-    const SceneDev &sc = P.scenes[scene];
-    SceneState &st = P.st[scene];
+    const SceneDev &sc = P.scenes[P.fblk_scene[blockIdx.x]];
     if (sc.nbody == 0) return;
     int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
     const bool valid = local < sc.nf;
@@ -129,10 +126,22 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int max_bodies)
         pi = P.pos_s[i];
         kt = (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
     }
-    // most blocks have no particle next to any boundary: write zero partials and skip
-    const bool any = __syncthreads_or(nb > 0) != 0;
+    // which bodies this block's particles touch (most blocks touch none, or only walls):
+    // untouched bodies get zero partials without a reduction
+    __shared__ unsigned long long s_mask;
+    if (threadIdx.x == 0) s_mask = 0ull;
+    __syncthreads();
+    unsigned long long mine = 0ull;
+    for (int t = 0; t < nb; ++t) {
+        const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * P.NF + i]];
+        if (k >= 0) mine |= 1ull << k;
+    }
+    if (mine) atomicOr(&s_mask, mine);
+    __syncthreads();
+    const unsigned long long touched = s_mask;
     for (int k = 0; k < sc.nbody; ++k) {
         double f[6] = {0, 0, 0, 0, 0, 0};
+        const bool any = (touched >> k) & 1ull;
         if (any) {
             const BodyDev &B = P.bodies[sc.body_off + k];
             for (int t = 0; t < nb; ++t) {
@@ -152,32 +161,33 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int max_bodies)
         }
         for (int a = 0; a < 6; ++a) {
             double t = any ? block_sum_d(f[a], sh) : 0.0;
-            if (threadIdx.x == 0) P.body_partial[((int64_t)blockIdx.x * max_bodies + k) * 6 + a] = t;
+            if (threadIdx.x == 0) P.body_partial[((int64_t)(sc.body_off + k) * 6 + a) * P.nfblk + blockIdx.x] = t;
         }
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        uint32_t prev = atomicAdd(&st.counter, 1u);
-        s_last = (prev == (uint32_t)sc.fblk_count - 1u);
-    }
+}
+
+// Sum of one body's force or torque component over its scene's fluid blocks, in block
+// order (one CUDA block per body and component).
+__global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
+{
+    __shared__ double sh[8];
+    const int body = blockIdx.x / 6, a = blockIdx.x % 6;
+    BodyDev &B = P.bodies[body];
+    const SceneDev &sc = P.scenes[B.scene];
+    const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.nfblk + sc.fblk_first;
+    double t = 0.0;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < sc.fblk_count; q += 256) t += part[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const volatile double *part = P.body_partial;
-    for (int k = 0; k < sc.nbody; ++k) {
-        for (int a = 0; a < 6; ++a) {
-            double t = 0.0;
-            for (int q = threadIdx.x; q < sc.fblk_count; q += kBlock)
-                t += part[((int64_t)(sc.fblk_first + q) * max_bodies + k) * 6 + a];
-            double tot = block_sum_d(t, sh);
-            if (threadIdx.x == 0) {
-                BodyDev &B = P.bodies[sc.body_off + k];
-                if (a < 3) B.force[a] = tot;
-                else B.torque[a - 3] = tot;
-            }
-        }
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += sh[w];
+        if (a < 3) B.force[a] = tot;
+        else B.torque[a - 3] = tot;
     }
-    if (threadIdx.x == 0) st.counter = 0;
 }
 
 }  // namespace
@@ -190,9 +200,13 @@ void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s)
 {
     if (P.nbblk) k_boundary_psi<<<P.nbblk, kBlock, 0, s>>>(P, only_moving);
 }
-void launch_body_force(const Ptrs &P, int max_bodies, cudaStream_t s)
+void launch_body_force(const Ptrs &P, cudaStream_t s)
 {
-    if (P.nfblk) k_body_force<<<P.nfblk, kBlock, 0, s>>>(P, max_bodies);
+    if (P.nfblk) k_body_force<<<P.nfblk, kBlock, 0, s>>>(P);
+}
+void launch_body_reduce(const Ptrs &P, cudaStream_t s)
+{
+    if (P.nbodies_total) k_body_reduce<<<P.nbodies_total * 6, 256, 0, s>>>(P);
 }
 
 }  // namespace sph

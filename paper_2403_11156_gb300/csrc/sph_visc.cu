@@ -1,0 +1,281 @@
+// sph_visc.cu -- implicit viscosity (Sec. 3.6.2): (I - dt A) v* = v~ solved by a
+// matrix-free conjugate gradient (Sec. 4.2 "conjugate gradient (matrix free)").
+//
+//   (A v)_i = sum_j A_ij (v_j - v_i),
+//   A_ij = -2(d+2) mu mbar_ij / (rho_i rho_j) grad W_ij x_ij^T / (|x_ij|^2 + 0.01 h^2),
+// d = 3, mbar = m (one particle mass per scene), mu = nu rho0.  The operator is applied
+// on the fly from the neighbour lists; the CG vectors live in float4 arrays whose w lane
+// keeps rho so that one gather serves both.  Dot products are accumulated per block in
+// FP64 and reduced in a fixed order by the last block of each scene; the loop runs on the
+// device (CUDA graph while node) until |r| <= tol |b| or cg_max_iter.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+__device__ __forceinline__ void count_launch(Control *ctl)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
+}
+
+__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
+{
+    if (!(r2 > 0.0f)) return 0.0f;
+    float rinv = rsqrtf(r2);
+    float q = r2 * rinv * sc.inv_h;
+    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
+    return sc.kgrad * g * rinv;
+}
+
+struct Ctx {
+    const SceneDev *sc;
+    SceneState *st;
+    int64_t i;
+    bool valid;
+};
+
+__device__ __forceinline__ Ctx ctx(const Ptrs &P)
+{
+    Ctx c;
+    int32_t s = P.fblk_scene[blockIdx.x];
+    c.sc = &P.scenes[s];
+    c.st = &P.st[s];
+    int64_t local = (int64_t)(blockIdx.x - c.sc->fblk_first) * kBlock + threadIdx.x;
+    c.valid = local < c.sc->nf;
+    c.i = c.sc->f_off + local;
+    return c;
+}
+
+// y = (I - dt A) x at particle i; X holds x in xyz and rho in w.
+__device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi, float4 xi,
+                                          const float4 *__restrict__ X, float dt)
+{
+    const int64_t NF = P.NF;
+    const int nn = P.nnf[i];
+    const float reg = 0.01f * sc.h2;
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    for (int k = 0; k < nn; ++k) {
+        const int32_t j = __ldg(P.nbr + (int64_t)k * NF + i);
+        const float4 pj = __ldg(P.pos_s + j);
+        const float4 xj = __ldg(X + j);
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // grad W_ij (x_ij . (x_j - x_i)) / (rho_j (r^2 + reg))
+        const float s = grad_factor(sc, r2) * (dx * (xj.x - xi.x) + dy * (xj.y - xi.y) + dz * (xj.z - xi.z)) /
+                        (xj.w * (r2 + reg));
+        ax = fmaf(s, dx, ax); ay = fmaf(s, dy, ay); az = fmaf(s, dz, az);
+    }
+    // (A x)_i = -10 mu m / rho_i * acc, so (I - dt A) x = x + dt 10 mu m / rho_i * acc
+    const float k = dt * 10.0f * sc.mu * sc.m / xi.w;
+    return make_float3(fmaf(k, ax, xi.x), fmaf(k, ay, xi.y), fmaf(k, az, xi.z));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block sums of two doubles (result in thread 0).
+__device__ void block_sum2(double &a, double &b, double *sh)
+{
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[2 * w] = a;
+        sh[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0;
+        b = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) {
+            a += sh[2 * k];
+            b += sh[2 * k + 1];
+        }
+    }
+}
+
+// Per-block partial sums, then the scene's last block sums them in block order.  Returns
+// true in thread 0 of the last block, with the totals in a and b.
+__device__ bool scene_reduce2(const Ptrs &P, const SceneDev &sc, SceneState &st, double &a, double &b,
+                              double *sh, int *s_last)
+{
+    block_sum2(a, b, sh);
+    if (threadIdx.x == 0) {
+        P.cg_dots[2 * blockIdx.x] = a;
+        P.cg_dots[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        uint32_t prev = atomicAdd(&st.counter, 1u);
+        *s_last = (prev == (uint32_t)sc.fblk_count - 1u);
+    }
+    __syncthreads();
+    if (!*s_last) return false;
+    __threadfence();
+    const volatile double *d = P.cg_dots;
+    double ta = 0.0, tb = 0.0;
+    for (int k = threadIdx.x; k < sc.fblk_count; k += kBlock) {
+        ta += d[2 * (sc.fblk_first + k)];
+        tb += d[2 * (sc.fblk_first + k) + 1];
+    }
+    block_sum2(ta, tb, sh);
+    a = ta;
+    b = tb;
+    if (threadIdx.x == 0) st.counter = 0;
+    return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ bool cg_active(const SceneDev &sc, const SceneState &st)
+{
+    return sc.visc_mode == 3 && st.cg_active != 0;
+}
+
+// x0 = v~ (already in vel_c), r0 = b - (I - dt A) x0, p0 = r0; |r0|^2 and |b|^2.
+__global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
+{
+    __shared__ double sh[2 * kBlock / 32];
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    Ctx c = ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    if (sc.visc_mode != 3) return;
+    double rr = 0.0, bb = 0.0;
+    if (c.valid) {
+        const int64_t i = c.i;
+        const float4 pi = P.pos_s[i];
+        const float4 xi = P.vel_c[i];
+        const float3 mx = apply_m(P, sc, i, pi, xi, P.vel_c, st.dt);
+        const float4 r = make_float4(xi.x - mx.x, xi.y - mx.y, xi.z - mx.z, xi.w);
+        P.cg_r[i] = r;
+        P.cg_p[i] = r;
+        rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+        bb = (double)xi.x * xi.x + (double)xi.y * xi.y + (double)xi.z * xi.z;
+    }
+    if (scene_reduce2(P, sc, st, rr, bb, sh, &s_last)) {
+        st.cg_rr = rr;
+        st.cg_bb = bb;
+        st.cg_it = 0;
+        const double tol = (double)sc.cg_tol;
+        st.cg_active = (sc.cg_max > 0 && rr > tol * tol * bb) ? 1 : 0;
+        st.cg_res = bb > 0.0 ? (float)sqrt(rr / bb) : 0.0f;
+    }
+}
+
+// Ap = (I - dt A) p; alpha = |r|^2 / p.Ap.
+__global__ void __launch_bounds__(kBlock) k_cg_ap(Ptrs P)
+{
+    __shared__ double sh[2 * kBlock / 32];
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    Ctx c = ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    if (!cg_active(sc, st)) return;
+    double pap = 0.0, unused = 0.0;
+    if (c.valid) {
+        const int64_t i = c.i;
+        const float4 pi = P.pos_s[i];
+        const float4 p = P.cg_p[i];
+        const float3 ap = apply_m(P, sc, i, pi, p, P.cg_p, st.dt);
+        P.cg_ap[i] = make_float4(ap.x, ap.y, ap.z, 0.0f);
+        pap = (double)p.x * ap.x + (double)p.y * ap.y + (double)p.z * ap.z;
+    }
+    if (scene_reduce2(P, sc, st, pap, unused, sh, &s_last)) st.cg_alpha = pap > 0.0 ? st.cg_rr / pap : 0.0;
+}
+
+// x += alpha p, r -= alpha Ap; beta = |r_new|^2 / |r|^2.
+__global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
+{
+    __shared__ double sh[2 * kBlock / 32];
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    Ctx c = ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    if (!cg_active(sc, st)) return;
+    double rr = 0.0, unused = 0.0;
+    if (c.valid) {
+        const int64_t i = c.i;
+        const float a = (float)st.cg_alpha;
+        const float4 p = P.cg_p[i];
+        const float4 ap = P.cg_ap[i];
+        float4 x = P.vel_c[i];
+        float4 r = P.cg_r[i];
+        x.x = fmaf(a, p.x, x.x); x.y = fmaf(a, p.y, x.y); x.z = fmaf(a, p.z, x.z);
+        r.x = fmaf(-a, ap.x, r.x); r.y = fmaf(-a, ap.y, r.y); r.z = fmaf(-a, ap.z, r.z);
+        P.vel_c[i] = x;
+        P.cg_r[i] = r;
+        rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+    }
+    if (scene_reduce2(P, sc, st, rr, unused, sh, &s_last)) {
+        st.cg_beta = st.cg_rr > 0.0 ? rr / st.cg_rr : 0.0;
+        st.cg_rr = rr;
+        st.cg_it += 1;
+        st.cg_res = st.cg_bb > 0.0 ? (float)sqrt(rr / st.cg_bb) : 0.0f;
+    }
+}
+
+// p = r + beta p; the last block of the launch decides whether any scene continues.
+__global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
+{
+    __shared__ int s_last;
+    count_launch(P.ctl);
+    Ctx c = ctx(P);
+    const SceneDev &sc = *c.sc;
+    SceneState &st = *c.st;
+    if (cg_active(sc, st) && c.valid) {
+        const int64_t i = c.i;
+        const float b = (float)st.cg_beta;
+        const float4 r = P.cg_r[i];
+        float4 p = P.cg_p[i];
+        p.x = fmaf(b, p.x, r.x); p.y = fmaf(b, p.y, r.y); p.z = fmaf(b, p.z, r.z);
+        P.cg_p[i] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        uint32_t prev = atomicAdd(&P.ctl->passb_counter, 1u);
+        s_last = (prev == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    uint32_t any = 0;
+    for (int s = 0; s < P.nscenes; ++s) {
+        const SceneDev &q = P.scenes[s];
+        SceneState &qs = P.st[s];
+        if (q.visc_mode != 3 || !qs.cg_active) continue;
+        const double tol = (double)q.cg_tol;
+        if (qs.cg_it >= q.cg_max || !(qs.cg_rr > tol * tol * qs.cg_bb)) qs.cg_active = 0;
+        else any = 1;
+    }
+    uint32_t guard = ++P.ctl->loop_guard;
+    if (guard > 100000u) {
+        any = 0;
+        P.ctl->error = 3;
+    }
+    if (!any) P.ctl->loop_guard = 0;
+    P.ctl->loop_flag = any;
+    P.ctl->passb_counter = 0;
+    __threadfence();
+    if (use_handle) cudaGraphSetConditional(handle, any);
+}
+
+}  // namespace
+
+void launch_cg_init(const Ptrs &P, cudaStream_t s) { k_cg_init<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_cg_ap(const Ptrs &P, cudaStream_t s) { k_cg_ap<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_cg_xr(const Ptrs &P, cudaStream_t s) { k_cg_xr<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
+{
+    k_cg_p<<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+}
+
+}  // namespace sph

@@ -1,0 +1,49 @@
+"""Run a named synthetic workload for a number of steps and print its statistics (JSON).
+
+    python -m paper_2403_11156_gb300.run_scene --scene rigid --steps 2 --eager
+
+Workloads: small (8k-particle dam break), rigid (1.2M-particle dam break with rigid boxes),
+column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k particles).
+--eager launches the kernels one by one (the form a kernel profiler can attribute);
+without it a step is one CUDA-graph launch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+from paper_2403_11156_gb300 import build, scenes, sph
+
+WORKLOADS = {
+    "small": lambda: [scenes.dam_break_small()],
+    "rigid": lambda: [scenes.dam_break_rigid()],
+    "column": lambda: [scenes.viscous_column()],
+    "batch": lambda: scenes.batch_dam_break(),
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scene", default="rigid", choices=sorted(WORKLOADS))
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--eager", action="store_true")
+    ap.add_argument("--dt", type=float, default=0.0)
+    args = ap.parse_args()
+    build.build()
+    descs = WORKLOADS[args.scene]()
+    g = sph.Context(descs, torch_allocator=False)
+    g.sph_set_mode(graph=not args.eager, timing=False)
+    t = time.perf_counter()
+    g.sph_steps(args.steps, args.dt)
+    status = g.sph_synchronize(raise_on_error=False)
+    el = time.perf_counter() - t
+    out = {"scene": args.scene, "scenes": len(descs), "steps": args.steps,
+           "fluid_particles": int(sum(len(d["fluid_x"]) for d in descs)),
+           "seconds": el, "status": sph.STATUS_NAMES[status], "stats": g.sph_get_stats(0)}
+    print(json.dumps(out))
+    g.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -129,10 +129,12 @@ def load():
     L.sph_last_error.argtypes = [vp]
     L.sph_destroy.argtypes = [vp]
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
+    L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
+    L.sph_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc"):
+                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -338,6 +340,10 @@ class Context:
         _check(self.ctx, load().sph_kernel_times(self.ctx, arr, cap, C.byref(n), int(reset)))
         return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(min(n.value, cap))}
 
+    def sph_set_mlp(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self.ctx, load().sph_set_mlp(self.ctx, _fptr(a), a.size))
+
     def sph_launch_count(self):
         n = C.c_int64()
         _check(self.ctx, load().sph_launch_count(self.ctx, C.byref(n)))
@@ -358,3 +364,15 @@ def sph_grid_order_noalloc(x, n, domain_min, domain_max, cell_size, order, keys=
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     return load().sph_grid_order_noalloc(ptr(x), int(n), lo, hi, float(cell_size), ptr(order),
                                          ptr(keys), st)
+
+
+MLP_PARAMS = 4555
+MLP_WEIGHTS = 4545
+
+
+def sph_mlp_forward(params, features, n, y, error, stream=None):
+    """Marshal sph_mlp_forward: device pointers (ints or tensors); returns the status."""
+    def ptr(t):
+        return None if t is None else (t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return load().sph_mlp_forward(ptr(params), ptr(features), int(n), ptr(y), ptr(error), st)

@@ -14,8 +14,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _scene():
-    # a small rigid dam break: 30 x 24 x 24 fluid, three boxes, r = 0.005
-    return scenes.dam_break_rigid(seed=9, n=(30, 24, 24), tank=(0.5, 0.25, 0.25), box_edge=0.04)
+    # a small rigid dam break: 30 x 22 x 22 fluid (1.1-spacing wall gaps on every side of
+    # the 0.25 m cross-section), three boxes in air, r = 0.005
+    return scenes.dam_break_rigid(seed=9, n=(30, 22, 22), tank=(0.5, 0.25, 0.35), box_edge=0.04)
 
 
 def _submerged():

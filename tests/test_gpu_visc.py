@@ -1,0 +1,58 @@
+"""GPU implicit viscosity (Sec. 3.6.2): the CUDA matrix-free CG's velocity v* must solve
+the oracle's system (I - dt A) v* = v~ (residual measured with the oracle's FP64
+operator on the same positions), agree with the oracle's own CG solution, and the
+column scene must run stably."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_11156_gb300 import scenes, sph
+
+from gpu_util import gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _column(**kw):
+    # 12 x 12 x 24 column (3,456 particles, several tiles plus a tail) above a plane
+    base = dict(n=(12, 12, 24), plane_size=0.2, max_iter_density=0, min_iter_density=0,
+                warm_start=0, divergence_solve=0)
+    base.update(kw)
+    return scenes.viscous_column(**base)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_cg_solves_oracle_system(tol):
+    d = _column(cg_tol=tol, cg_max_iter=1000)
+    rng = np.random.default_rng(1)
+    d["fluid_v"] = (0.3 * rng.normal(size=d["fluid_x"].shape)).astype(np.float32)
+    dt = 1e-3
+    g = gpu_ctx(d)
+    g.sph_step(dt)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    v_gpu = g.sph_read_state()[1].astype(np.float64)
+    st = g.sph_get_stats()
+    assert st["cg_iters"] > 1 and st["cg_residual"] <= tol * 1.0001
+    o = oracle.Scene(d)
+    o.prepare()
+    b = d["fluid_v"].astype(np.float64) + dt * np.array(d["gravity"])
+    res = o.visc_operator(dt, v_gpu) - b
+    # the FP32 iterate solves the FP64 system to the CG tolerance plus the FP32 rounding
+    # of the operator itself (about 5e-6 of |b| here, so the floor is 1e-5)
+    assert np.linalg.norm(res) <= (tol + 1e-5) * np.linalg.norm(b)
+    o.step(dt)
+    v_ref = o.get(oracle.V)
+    assert np.abs(v_gpu - v_ref).max() <= 20 * (tol + 1e-5) * np.abs(b).max()
+
+
+def test_column_runs():
+    d = scenes.viscous_column(n=(16, 16, 32), plane_size=0.3)
+    g = gpu_ctx(d)
+    g.sph_steps(30, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) in (sph.SPH_OK, sph.SPH_ENOCONVERGE)
+    st = g.sph_get_stats()
+    # a column in free fall is nearly rigid (A v ~ 0), so few or no CG iterations
+    assert st["cg_residual"] <= 1e-4 * 1.0001
+    x, v, rho, p = g.sph_read_state()
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    assert x[:, 2].min() > -0.01                     # the plane holds the column
