@@ -245,6 +245,25 @@ sph_status sph_set_mlp(sph_ctx *ctx, const float *params, int64_t n);
 sph_status sph_mlp_forward(const float *params, const float *features, int64_t n, float *y,
                            int32_t *error, void *stream);
 
+/* Gradient of the mean squared error (1/n) sum (y - label)^2 of the network over n
+ * standardised samples (device arrays: features [n][4], labels [n]) with respect to the
+ * first SPH_MLP_WEIGHTS parameters -> grad (device float [SPH_MLP_WEIGHTS]); *loss (device
+ * double) receives the sum of squared errors.  BF16 tensor-core forward and backward with
+ * FP32 accumulation.  *error (device int32) is set to 1 if a tensor-core wait gave up. */
+sph_status sph_mlp_grad(const float *params, const float *features, const float *labels, int64_t n,
+                        float *grad, double *loss, int32_t *error, void *stream);
+
+/* Train the network on raw (unstandardised) samples, device arrays features [n][4] and
+ * labels [n]: the call computes the standardisation statistics into params, then runs
+ * `epochs` passes of Adam (lr, beta = 0.9/0.999, eps = 1e-8) over mini-batches of
+ * `batch` samples in a seeded per-epoch order, updating params (device, FP32 master
+ * weights) and adam_state (device float [2 * SPH_MLP_WEIGHTS], zero for a fresh start).
+ * loss_history (device float [epochs], may be NULL) receives each epoch's mean squared
+ * error in standardised units.  Allocates its scratch with cudaMallocAsync on stream. */
+sph_status sph_mlp_train(const float *features, const float *labels, int64_t n, float *params,
+                         float *adam_state, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                         float *loss_history, int32_t *error, void *stream);
+
 /* Kernel launches enqueued since creation (counted on the device for graph replays). */
 sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
 

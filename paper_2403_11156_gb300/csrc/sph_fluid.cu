@@ -522,17 +522,19 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     const float rho = vi.w;
     const float D = drho_dt(P, sc, i, pi, vi, P.vel_c);
     const float dev = fmaf(dt, D, rho - sc.rho0);
+    // the network's inputs are recorded in both warm-start modes (the previous-step mode
+    // produces the training data)
+    const float kref = 9.81f * sc.h;
+    float4 f;
+    f.x = rho / sc.rho0 - 1.0f;
+    f.y = dt * D / sc.rho0;
+    f.z = (float)(P.nnf[i] + P.nnb[i]) / 33.0f;
+    f.w = P.kprev_s[i] / (dt * dt) / kref;
+    reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;
     if (sc.warm == 1) {
         if (dev > 0.0f) k0 = 0.5f * P.kprev_s[i] / (dt * dt);
     } else if (P.ctl->have_mlp) {
-        const float kref = 9.81f * sc.h;
-        float4 f;
-        f.x = rho / sc.rho0 - 1.0f;
-        f.y = dt * D / sc.rho0;
-        f.z = (float)(P.nnf[i] + P.nnb[i]) / 33.0f;
-        f.w = P.kprev_s[i] / (dt * dt) / kref;
-        reinterpret_cast<float4 *>(P.feat)[i] = f;
         k0 = dev > 0.0f ? 1.0f : 0.0f;   // gate; the network kernel replaces it
     }
     P.k0[i] = k0;

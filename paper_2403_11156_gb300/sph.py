@@ -131,10 +131,12 @@ def load():
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
     L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
     L.sph_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    L.sph_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.sph_mlp_train.argtypes = [vp, vp, C.c_int64, vp, vp, ip, ip, C.c_float, C.c_uint64, vp, vp, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward"):
+                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -311,6 +313,11 @@ class Context:
         _check(self.ctx, load().sph_write_state(self.ctx, scene, arr(x, (n, 3)), arr(v, (n, 3)),
                                                 arr(kappa_prev, (n,)), arr(kappa_v_prev, (n,)), 0))
 
+    def sph_read_field_device(self, field, out, scene=0):
+        """Write a per-particle field into a caller-owned device buffer (tensor or pointer)."""
+        _check(self.ctx, load().sph_read_field(self.ctx, scene, field, _dptr(out), 1))
+        return out
+
     def sph_read_field(self, field, scene=0):
         dt, w, boundary = FIELD_LAYOUT[field]
         n = self.n_boundary[scene] if boundary else self.n_fluid[scene]
@@ -376,3 +383,25 @@ def sph_mlp_forward(params, features, n, y, error, stream=None):
         return None if t is None else (t.data_ptr() if hasattr(t, "data_ptr") else int(t))
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     return load().sph_mlp_forward(ptr(params), ptr(features), int(n), ptr(y), ptr(error), st)
+
+
+def _dptr(t):
+    return None if t is None else (t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+
+
+def _sptr(stream):
+    return None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def sph_mlp_grad(params, features, labels, n, grad, loss, error, stream=None):
+    """Marshal sph_mlp_grad (device pointers or tensors); returns the status."""
+    return load().sph_mlp_grad(_dptr(params), _dptr(features), _dptr(labels), int(n), _dptr(grad),
+                               _dptr(loss), _dptr(error), _sptr(stream))
+
+
+def sph_mlp_train(features, labels, n, params, adam_state, epochs, batch, lr, seed, loss_history,
+                  error, stream=None):
+    """Marshal sph_mlp_train (device pointers or tensors); returns the status."""
+    return load().sph_mlp_train(_dptr(features), _dptr(labels), int(n), _dptr(params),
+                                _dptr(adam_state), int(epochs), int(batch), float(lr), int(seed),
+                                _dptr(loss_history), _dptr(error), _sptr(stream))

@@ -59,3 +59,56 @@ def test_forward_matches_oracle(n):
     # and 1e-3 of the same network with BF16-rounded operands (catches layout errors)
     emu = _bf16_reference(p.astype(np.float32).astype(np.float64), f.astype(np.float32))
     np.testing.assert_allclose(yg, emu, rtol=0, atol=1e-3 * np.abs(emu).max())
+
+
+def test_gradient_matches_oracle():
+    import torch
+    rng = np.random.default_rng(11)
+    n = 1000
+    p = _params(rng, 0.3)
+    f = rng.normal(size=(n, 4)).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    dev = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device="cuda")
+    g = torch.zeros(sph.MLP_WEIGHTS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert sph.sph_mlp_grad(dev(p), dev(f), dev(t), n, g, loss, err) == sph.SPH_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    p64 = p.astype(np.float32).astype(np.float64)
+    ref_loss, ref_g = oracle.mlp_loss_grad(p64, f.astype(np.float64), t.astype(np.float64))
+    assert float(loss.item()) / n == pytest.approx(ref_loss, rel=2e-2)
+    gg = g.cpu().numpy().astype(np.float64)
+    # BF16 operands: normwise 2e-2 overall and per parameter group
+    assert np.linalg.norm(gg - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
+    for lo, hi in [(0, 256), (256, 320), (320, 4416), (4416, 4480), (4480, 4544), (4544, 4545)]:
+        assert np.linalg.norm(gg[lo:hi] - ref_g[lo:hi]) <= 5e-2 * np.linalg.norm(ref_g[lo:hi]) + 1e-7
+
+
+def test_training_fits():
+    import torch
+    rng = np.random.default_rng(12)
+    n = 4096
+    f = rng.normal(size=(n, 4)).astype(np.float32) * np.array([1.0, 3.0, 0.5, 2.0], np.float32) + 1.0
+    t = (np.sin(f[:, 0]) + 0.3 * f[:, 1] * f[:, 2] - 0.2 * f[:, 3]).astype(np.float32)
+    p = _params(rng, 0.2)
+    dp = torch.tensor(p, dtype=torch.float32, device="cuda")
+    adam = torch.zeros(2 * sph.MLP_WEIGHTS, dtype=torch.float32, device="cuda")
+    epochs = 60
+    hist = torch.zeros(epochs, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = sph.sph_mlp_train(torch.tensor(f, device="cuda"), torch.tensor(t, device="cuda"), n, dp, adam,
+                           epochs, 256, 3e-3, 7, hist, err)
+    assert st == sph.SPH_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    h = hist.cpu().numpy()
+    assert h[-1] < 0.05 * h[0] and h[-1] < 0.05
+    # the standardisation statistics went into the parameter block
+    pp = dp.cpu().numpy()
+    np.testing.assert_allclose(pp[sph.MLP_WEIGHTS:sph.MLP_WEIGHTS + 4], f.mean(0), rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(pp[sph.MLP_WEIGHTS + 4:sph.MLP_WEIGHTS + 8], f.std(0), rtol=1e-3)
+    # the trained network predicts the training targets (oracle forward on its weights)
+    fs = (f - pp[sph.MLP_WEIGHTS:sph.MLP_WEIGHTS + 4]) / pp[sph.MLP_WEIGHTS + 4:sph.MLP_WEIGHTS + 8]
+    y = oracle.mlp_forward(pp.astype(np.float64), fs.astype(np.float64)) * pp[-1] + pp[-2]
+    assert np.mean((y - t) ** 2) < 0.1 * np.var(t)

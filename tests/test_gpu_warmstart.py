@@ -1,0 +1,77 @@
+"""Learned warm start end to end on the GPU: training data from the solver's own steps,
+GPU training, and the in-step network prediction kappa0 against the oracle's FP64
+network with the same weights (BF16 tensor-core layers: normwise 3e-2 of kappa0; the
+compression gate rho* > rho0 is decided in FP32 vs FP64 and may differ on particles at
+rest density)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_11156_gb300 import scenes, sph, warmstart
+
+from gpu_util import forced, gpu_ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import torch
+    rng = np.random.default_rng(3)
+    feats, labels = [], []
+    d = scenes.dam_break_random(41, 40_000)
+    n = len(d["fluid_x"])
+    kref = 9.81 * 4.0 * d["radius"]
+    with sph.Context(d) as g:
+        f = torch.empty((n, 4), device="cuda")
+        k = torch.empty(n, device="cuda")
+        for _ in range(40):
+            g.sph_step(0.0)
+            g.sph_read_field_device(sph.FIELD_FEATURES, f)
+            g.sph_read_field_device(sph.FIELD_KAPPA, k)
+            idx = torch.from_numpy(rng.choice(n, 500, replace=False)).cuda()
+            feats.append(f[idx].clone())
+            labels.append(k[idx] / kref)
+    F, Y = torch.cat(feats), torch.cat(labels)
+    params, hist = warmstart.train(F, Y, epochs=20, batch=1024, lr=2e-3)
+    return params, hist
+
+
+def test_training_on_solver_states(trained):
+    params, hist = trained
+    assert np.all(np.isfinite(hist)) and hist[-1] < hist[0]
+    assert np.all(np.isfinite(params))
+
+
+def test_learned_kappa0_matches_oracle(trained):
+    params, _ = trained
+    d = forced(scenes.dam_break_small(warm_start=scenes.WARM_LEARNED), 1, 2)
+    g = gpu_ctx(d)
+    g.sph_set_mlp(params)
+    o = oracle.Scene(d)
+    o.set_mlp(params.astype(np.float64))
+    dt = 4e-4
+    for _ in range(3):                          # build warm-start memory on the GPU
+        g.sph_step(dt)
+    x, v, _, _ = g.sph_read_state()
+    o.set_state(x, v, g.sph_read_field(sph.FIELD_KAPPA_PREV), g.sph_read_field(sph.FIELD_KAPPA_V_PREV))
+    g.sph_step(dt)
+    g.sph_synchronize(raise_on_error=False)
+    o.step(dt)
+    kg = g.sph_read_field(sph.FIELD_KAPPA0).astype(np.float64)
+    ko = o.get(oracle.KAPPA0)
+    np.testing.assert_allclose(g.sph_read_field(sph.FIELD_FEATURES), o.get(oracle.FEAT),
+                               rtol=1e-3, atol=1e-4)
+    gate_g, gate_o = kg > 0, ko > 0
+    assert np.mean(gate_g != gate_o) < 0.01
+    both = gate_g & gate_o
+    assert both.sum() > 100
+    assert np.linalg.norm(kg[both] - ko[both]) <= 3e-2 * np.linalg.norm(ko[both])
+
+
+def test_learned_mode_runs(trained):
+    params, _ = trained
+    res = warmstart.compare_warm_starts(scenes.dam_break_small(), params, steps=20)
+    for mode in ("zero", "previous", "learned"):
+        assert res[mode]["final_error"] <= 1e-3 or res[mode]["density_iters_per_step"] >= 100
+        assert res[mode]["density_iters_per_step"] >= 2
