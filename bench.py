@@ -120,6 +120,27 @@ def cpu_baseline(desc, steps=2):
                       "(FP64, OpenMP, %.1f s)" % (steps, n, el)}
 
 
+def learned_vs_plain():
+    """Train the warm-start network on the GPU from the solver's own states (200k samples
+    from 500 steps of seeded 0.5M-1.2M-particle dam breaks) and compare the zero,
+    previous-step and learned warm starts on the 8k-particle dam break (100 steps, fixed
+    dt = 4e-4 s) at the 0.1 % tolerance and at 0.001 %."""
+    import time as _t
+    from paper_2403_11156_gb300 import scenes, warmstart
+    t = _t.perf_counter()
+    f, y = warmstart.generate_dataset(200_000, 500)
+    t_data = _t.perf_counter() - t
+    t = _t.perf_counter()
+    params, hist = warmstart.train(f, y, epochs=30)
+    t_train = _t.perf_counter() - t
+    out = {"samples": int(f.shape[0]), "data_s": round(t_data, 3), "train_s": round(t_train, 3),
+           "train_loss_first": float(hist[0]), "train_loss_last": float(hist[-1])}
+    for tag, eta in (("eta_1e-3", 1e-3), ("eta_1e-5", 1e-5)):
+        desc = scenes.dam_break_small(eta_density=eta, eta_divergence=eta)
+        out[tag] = warmstart.compare_warm_starts(desc, params, steps=100)
+    return out
+
+
 def reference_sample():
     from paper_2403_11156_gb300 import scenes
     # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
@@ -163,6 +184,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timing-steps", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default 27-cell stencil and gather batch instead of autotuning")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain warm-start comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -189,7 +214,8 @@ def main():
     desc = scenes.dam_break_rigid()
     n_fluid = len(desc["fluid_x"])
     stream = torch.cuda.Stream()
-    g = sph.Context(desc, stream=stream)
+    g = sph.Context(desc, stream=stream, autotune=not args.no_autotune)
+    tuning = g.sph_get_tuning()
     g.sph_steps(args.warmup, 0.0)
     g.sph_synchronize()
 
@@ -267,6 +293,10 @@ def main():
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4)}
                  for k, v in sorted(kt.items(), key=lambda t: -t[1][1])}
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_vs_plain()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g.close()
@@ -283,9 +313,10 @@ def main():
                    "warm_start": "previous-step kappa (plain DFSPH)",
                    "l2": "working set per step > L2 (129 MB); no flush",
                    "mean_density_iters": d_it / args.steps, "mean_divergence_iters": v_it / args.steps,
-                   "final_density_error": it1["dens_err"], "dt": it1["dt"], "status": sph.STATUS_NAMES[status]},
+                   "final_density_error": it1["dens_err"], "dt": it1["dt"], "status": sph.STATUS_NAMES[status],
+                   "autotune": tuning},
         "clocks": clocks.summary(), "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
-        "kernels": breakdown, "cpu_baseline": cpu,
+        "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -84,7 +84,8 @@ typedef struct sph_scene_desc {
     float gravity[3];             /* m/s^2                                            */
     float domain_min[3];          /* grid extent; particles outside are clamped into  */
     float domain_max[3];          /* the edge cells (still correct, only slower)      */
-    float cell_size;              /* 0 = h (1 + 2^-8); otherwise >= that value        */
+    float cell_size;              /* 0 = h (1 + 2^-8) (27-cell stencil); >= h/2 (1 +  */
+                                  /* 2^-8) for a 125-cell stencil; < 0 = autotune     */
     float eta_density;            /* mean relative density error tolerance (1e-3)     */
     float eta_divergence;         /* mean dt Drho/Dt / rho0 tolerance (1e-3)          */
     float dt_max;                 /* largest step, s                                  */
@@ -213,6 +214,25 @@ sph_status sph_read_bodies(sph_ctx *ctx, int32_t scene, double *out);
  * timing != 0 (eager mode only) brackets every kernel with CUDA events on the context
  * stream. */
 sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
+
+/* Autotuning.  A scene created with cell_size < 0 lets sph_create choose its grid cell
+ * size (h (1 + 2^-8), 27-cell stencil, or h/2 (1 + 2^-8), 125-cell stencil) and the
+ * number of neighbours each thread keeps in flight in the Jacobi passes (4 or 8) by
+ * timing a few CUDA-graph steps of every candidate on temporary contexts; the choice is
+ * cached per process for the same device and workload size (log2 of the fluid count,
+ * scene count, bodies, viscosity mode).  Neighbour sets do not depend on the choice;
+ * the summation order, and so the last bits of FP32 results, may. */
+typedef struct sph_tuning {
+    int32_t tuned;            /* 1 if this context was autotuned                     */
+    int32_t from_cache;       /* the choice came from the per-process cache          */
+    int32_t gather_batch;     /* chosen neighbours in flight per thread              */
+    float cell_factor;        /* chosen cell size / h                                */
+    int32_t n_trials;
+    float trial_cell_factor[8];
+    int32_t trial_batch[8];
+    float trial_ms[8];        /* mean milliseconds per step of each candidate        */
+} sph_tuning;
+sph_status sph_get_tuning(sph_ctx *ctx, sph_tuning *out);
 
 /* Per-kernel timing collected in eager timing mode: up to cap entries of name (63
  * chars + NUL), launches and total milliseconds; returns the entry count in *n. */

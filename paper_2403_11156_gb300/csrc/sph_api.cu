@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,8 @@ struct sph_ctx {
     int64_t host_launches = 0;
 
     std::vector<int32_t> reported_flags;
+    int batch = 4;                       // neighbours in flight per thread in the Jacobi passes
+    sph_tuning tuning{};
     uint32_t *h_flag = nullptr;          // pinned word for eager loop control
 };
 
@@ -119,6 +122,13 @@ float default_cell(float radius)
     return h * 1.00390625f;
 }
 
+// smallest cell the 5 x 5 x 5 stencil supports: h/2 (1 + 2^-8)
+float half_cell(float radius)
+{
+    float h = 4.0f * radius;
+    return h * 0.501953125f;
+}
+
 sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
 {
     auto bad = [&](const char *what) { return fail(c, SPH_EINVAL, "scene %d: %s", idx, what); };
@@ -147,7 +157,8 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.warm_start < 0 || d.warm_start > 2) return bad("warm_start");
     if (d.max_fluid_neighbors < 0 || d.max_fluid_neighbors > 1024) return bad("max_fluid_neighbors");
     if (d.max_boundary_neighbors < 0 || d.max_boundary_neighbors > 1024) return bad("max_boundary_neighbors");
-    if (d.cell_size != 0.0f && !(d.cell_size >= default_cell(d.radius))) return bad("cell_size below h (1 + 2^-8)");
+    if (d.cell_size > 0.0f && !(d.cell_size >= half_cell(d.radius))) return bad("cell_size below h/2 (1 + 2^-8)");
+    if (!std::isfinite(d.cell_size)) return bad("cell_size not finite");
     if (d.n_bodies < 0 || d.n_bodies > SPH_MAX_BODIES) return bad("n_bodies out of range");
     if (d.n_bodies > 0 && !d.bodies) return bad("bodies is NULL");
     for (int k = 0; k < d.n_bodies; ++k) {
@@ -166,7 +177,7 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
             return bad("non-finite fluid input");
     for (int64_t i = 0; i < 3 * d.n_boundary; ++i)
         if (!std::isfinite(d.boundary_x[i])) return bad("non-finite boundary input");
-    float c0 = d.cell_size > 0.0f ? d.cell_size : default_cell(d.radius);
+    float c0 = d.cell_size > 0.0f ? d.cell_size : half_cell(d.radius);
     double cells = 1.0;
     for (int a = 0; a < 3; ++a) {
         float ext = (d.domain_max[a] - d.domain_min[a]) / c0;
@@ -421,14 +432,14 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         const char *na = solver == 0 ? "div_pass_a" : "dens_pass_a";
         const char *nb = solver == 0 ? "div_pass_b" : "dens_pass_b";
         return device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
-            run(c, q, na, [&] { launch_pass_a(P, solver, q); });
-            run(c, q, nb, [&] { launch_pass_b(P, solver, 0, h, use, q); });
+            run(c, q, na, [&] { launch_pass_a(P, solver, c->batch, q); });
+            run(c, q, nb, [&] { launch_pass_b(P, solver, 0, c->batch, h, use, q); });
         });
     };
 
     sph_status st;
     if (c->any_div) {
-        if (c->any_warm_div) run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, 0, 0, s); });
+        if (c->any_warm_div) run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, 0, 0, s); });
         if ((st = loop(0)) != SPH_OK) return st;
     }
     run(c, s, "nonpressure", [&] { launch_nonpressure(P, s); });
@@ -444,7 +455,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     if (c->any_warm) {
         run(c, s, "warm_density", [&] { launch_warm_density(P, s); });
         if (c->any_learned) run(c, s, "mlp_warm", [&] { launch_mlp_warm(P, s); });
-        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, 0, 0, s); });
+        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, 0, 0, s); });
     }
     if ((st = loop(1)) != SPH_OK) return st;
     if (c->any_bodies) {
@@ -488,7 +499,7 @@ sph_status check_async(sph_ctx *c)
 }
 
 sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocator *alloc, void *stream,
-                       sph_ctx **out)
+                       sph_ctx **out, int batch = 4)
 {
     if (!out) return SPH_EINVAL;
     *out = nullptr;
@@ -502,6 +513,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         return SPH_EINVAL;
     }
     c->stream = (cudaStream_t)stream;
+    c->batch = batch == 8 ? 8 : 4;
     if (alloc && alloc->alloc && alloc->free) {
         c->alloc = *alloc;
         c->use_alloc = true;
@@ -532,6 +544,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.nb = d.n_boundary;
         q.c_off = NC;
         q.cell = d.cell_size > 0.0f ? d.cell_size : default_cell(d.radius);
+        q.R = q.cell >= default_cell(d.radius) ? 1 : 2;
         int64_t nc = 1;
         for (int a = 0; a < 3; ++a) {
             q.origin[a] = d.domain_min[a] - q.cell;
@@ -793,6 +806,104 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     return SPH_OK;
 }
 
+// ------------------------------------------------------------------ autotuning
+std::mutex g_tune_mu;
+std::map<std::string, sph_tuning> g_tune_cache;
+
+std::string tune_key(const sph_scene_desc *d, int32_t n)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    char name[256] = "unknown";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) snprintf(name, sizeof name, "%s", prop.name);
+    int64_t nf = 0;
+    for (int s = 0; s < n; ++s) nf += d[s].n_fluid;
+    int bucket = 0;
+    while ((int64_t)1 << (bucket + 1) <= nf) ++bucket;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|fluid2^%d|scenes%d|bodies%d|visc%d", name, bucket, n, d[0].n_bodies,
+             d[0].viscosity_mode);
+    return buf;
+}
+
+// Time `steps` CUDA-graph steps of one configuration on a temporary context.
+sph_status time_config(const std::vector<sph_scene_desc> &descs, const sph_allocator *alloc, void *stream,
+                       int batch, int steps, float *ms)
+{
+    sph_ctx *t = nullptr;
+    sph_status st = create_impl(descs.data(), (int32_t)descs.size(), alloc, stream, &t, batch);
+    if (st != SPH_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    st = sph_steps(t, 2, 0.0f);
+    if (st == SPH_OK) {
+        cudaEventRecord(a, s);
+        st = sph_steps(t, steps, 0.0f);
+        cudaEventRecord(b, s);
+    }
+    if (st == SPH_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(ms, a, b);
+    else if (st == SPH_OK) st = SPH_ECUDA;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sph_destroy(t);
+    *ms /= (float)steps;
+    return st;
+}
+
+// Scenes with cell_size < 0: pick the cell size (27- or 125-cell stencil) and the gather
+// batch by timing each candidate, cache the choice, and build the context with it.
+sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_allocator *alloc, void *stream,
+                        sph_ctx **out)
+{
+    std::vector<sph_scene_desc> trial(descs, descs + n);
+    const std::string key = tune_key(descs, n);
+    sph_tuning best{};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        const float factors[2] = {1.00390625f, 0.501953125f};
+        const int batches[2] = {4, 8};
+        float best_ms = 1e30f;
+        best.n_trials = 0;
+        for (int f = 0; f < 2; ++f)
+            for (int b = 0; b < 2; ++b) {
+                for (int s = 0; s < n; ++s)
+                    trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * factors[f] : descs[s].cell_size;
+                float ms = 0.0f;
+                sph_status st = time_config(trial, alloc, stream, batches[b], 5, &ms);
+                if (st != SPH_OK) return st;
+                const int k = best.n_trials++;
+                best.trial_cell_factor[k] = factors[f];
+                best.trial_batch[k] = batches[b];
+                best.trial_ms[k] = ms;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.cell_factor = factors[f];
+                    best.gather_batch = batches[b];
+                }
+            }
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    best.tuned = 1;
+    best.from_cache = cached ? 1 : 0;
+    for (int s = 0; s < n; ++s)
+        trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * best.cell_factor : descs[s].cell_size;
+    sph_status st = create_impl(trial.data(), n, alloc, stream, out, best.gather_batch);
+    if (st == SPH_OK) (*out)->tuning = best;
+    return st;
+}
+
 sph_status check_ctx(sph_ctx *c)
 {
     if (!c) return SPH_EINVAL;
@@ -807,15 +918,47 @@ extern "C" {
 
 int32_t sph_abi_version(void) { return SPH_ABI_VERSION; }
 
+static bool wants_tuning(const sph_scene_desc *d, int32_t n)
+{
+    for (int s = 0; d && s < n; ++s)
+        if (d[s].cell_size < 0.0f) return true;
+    return false;
+}
+
 sph_status sph_create(const sph_scene_desc *scene, const sph_allocator *alloc, void *stream, sph_ctx **out)
 {
-    return create_impl(scene, 1, alloc, stream, out);
+    return sph_create_batch(scene, 1, alloc, stream, out);
 }
 
 sph_status sph_create_batch(const sph_scene_desc *scenes, int32_t n, const sph_allocator *alloc, void *stream,
                             sph_ctx **out)
 {
+    if (wants_tuning(scenes, n)) {
+        // validate once (a negative cell size is the tuning request)
+        std::vector<sph_scene_desc> v(scenes, scenes + n);
+        for (auto &d : v)
+            if (d.cell_size < 0.0f) d.cell_size = 0.0f;
+        sph_ctx probe;
+        for (int s = 0; s < n; ++s) {
+            sph_status st = validate(&probe, v[s], s);
+            if (st != SPH_OK) return st;
+        }
+        return create_tuned(scenes, n, alloc, stream, out);
+    }
     return create_impl(scenes, n, alloc, stream, out);
+}
+
+sph_status sph_get_tuning(sph_ctx *c, sph_tuning *out)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (!out) return fail(c, SPH_EINVAL, "out is NULL");
+    *out = c->tuning;
+    if (!c->tuning.tuned) {
+        out->gather_batch = c->batch;
+        out->cell_factor = c->scenes[0].cell / (4.0f * (float)(c->scenes[0].two_r * 0.5f));
+    }
+    return SPH_OK;
 }
 
 sph_status sph_step(sph_ctx *c, float dt)

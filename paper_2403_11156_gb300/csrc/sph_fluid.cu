@@ -179,18 +179,19 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         const int32_t cx = cell_coord(pi.x, sc.origin[0], sc.cell, sc.dims[0]);
         const int32_t cy = cell_coord(pi.y, sc.origin[1], sc.cell, sc.dims[1]);
         const int32_t cz = cell_coord(pi.z, sc.origin[2], sc.cell, sc.dims[2]);
-        const int32_t x0 = max(cx - 1, 0), x1 = min(cx + 1, sc.dims[0] - 1);
+        const int32_t R = sc.R;
+        const int32_t x0 = max(cx - R, 0), x1 = min(cx + R, sc.dims[0] - 1);
         const float h2 = sc.h2;
         const int cap_f = sc.cap_f, cap_b = sc.cap_b;
         int32_t *__restrict__ nbr = P.nbr;
         int32_t *__restrict__ bnbr = P.bnbr;
-        // phase 1: the float predicate over the 27-cell stencil (9 contiguous index
-        // ranges) only records neighbours; keeping the expensive per-pair work out of this
+        // phase 1: the float predicate over the (2R+1)^3-cell stencil ((2R+1)^2
+        // contiguous index ranges) only records neighbours; keeping the expensive per-pair work out of this
         // loop keeps the warp converged while most candidates are rejected
-        for (int32_t dz = -1; dz <= 1; ++dz) {
+        for (int32_t dz = -R; dz <= R; ++dz) {
             const int32_t z = cz + dz;
             if (z < 0 || z >= sc.dims[2]) continue;
-            for (int32_t dy = -1; dy <= 1; ++dy) {
+            for (int32_t dy = -R; dy <= R; ++dy) {
                 const int32_t y = cy + dy;
                 if (y < 0 || y >= sc.dims[1]) continue;
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
@@ -283,12 +284,13 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
 // (SPH divergence of Sec. 3.2 in the continuity equation, boundary per Sec. 3.5).
 constexpr int kBatch = 4;
 
+template <int B = kBatch>
 __device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi,
                                          float4 vi, const float4 *__restrict__ V)
 {
     const int64_t NF = P.NF;
     float acc = 0.0f;
-    for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+    for_list<B>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
         const float4 pj = __ldg(P.pos_s + j);
         const float4 vj = __ldg(V + j);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -315,7 +317,7 @@ __device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int6
 // Pass A of a Jacobi iteration (Alg. ppe_solver "refine p"): the source term of
 // Eq. velocity_source (solver 0) or Eq. density_source with rho* (solver 1), the
 // stiffness kappa_i = alpha_i e_i / dt^(1 or 2), and the block's FP64 error partial.
-template <int S>
+template <int S, int B>
 __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
         const float4 pi = P.pos_s[i];
         const float4 vi = V[i];
         const float rho = vi.w;
-        const float D = drho_dt(P, sc, i, pi, vi, V);
+        const float D = drho_dt<B>(P, sc, i, pi, vi, V);
         float ei, kappa;
         if (S == 0) {
             ei = fmaxf(D, 0.0f);
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 // Eq. rigid_pressure per unit fluid mass:
 //   v_i -= dt [ sum_j m (k_i/rho_i + k_j/rho_j) grad W_ij + sum_b Psi_b (k_i/rho_i) grad W_ib ]
 // WARM = 1 applies the warm-start kappas (no loop bookkeeping).
-template <int S, int WARM>
+template <int S, int WARM, int B>
 __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
 {
     __shared__ int s_last;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
         const float4 pi = P.pos_s[i];
         const float ki = pi.w;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+        for_list<B>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
             const float4 pj = __ldg(P.pos_s + j);
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
@@ -659,21 +661,28 @@ void launch_step_begin(const Ptrs &P, cudaStream_t s)
     k_step_begin<<<b, t, 0, s>>>(P);
 }
 void launch_density_alpha(const Ptrs &P, cudaStream_t s) { k_density_alpha<<<P.nfblk, kBlock, 0, s>>>(P); }
-void launch_pass_a(const Ptrs &P, int solver, cudaStream_t s)
+void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s)
 {
-    if (solver == 0) k_pass_a<0><<<P.nfblk, kBlock, 0, s>>>(P);
-    else k_pass_a<1><<<P.nfblk, kBlock, 0, s>>>(P);
+    if (batch == 8) {
+        if (solver == 0) k_pass_a<0, 8><<<P.nfblk, kBlock, 0, s>>>(P);
+        else k_pass_a<1, 8><<<P.nfblk, kBlock, 0, s>>>(P);
+    } else {
+        if (solver == 0) k_pass_a<0, 4><<<P.nfblk, kBlock, 0, s>>>(P);
+        else k_pass_a<1, 4><<<P.nfblk, kBlock, 0, s>>>(P);
+    }
 }
-void launch_pass_b(const Ptrs &P, int solver, int warm, cudaGraphConditionalHandle h, int use_handle,
+void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphConditionalHandle h, int use_handle,
                    cudaStream_t s)
 {
-    if (solver == 0) {
-        if (warm) k_pass_b<0, 1><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
-        else k_pass_b<0, 0><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+#define SPH_PASS_B(S, W, B) k_pass_b<S, W, B><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle)
+    if (batch == 8) {
+        if (solver == 0) { if (warm) SPH_PASS_B(0, 1, 8); else SPH_PASS_B(0, 0, 8); }
+        else { if (warm) SPH_PASS_B(1, 1, 8); else SPH_PASS_B(1, 0, 8); }
     } else {
-        if (warm) k_pass_b<1, 1><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
-        else k_pass_b<1, 0><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+        if (solver == 0) { if (warm) SPH_PASS_B(0, 1, 4); else SPH_PASS_B(0, 0, 4); }
+        else { if (warm) SPH_PASS_B(1, 1, 4); else SPH_PASS_B(1, 0, 4); }
     }
+#undef SPH_PASS_B
 }
 void launch_nonpressure(const Ptrs &P, cudaStream_t s) { k_nonpressure<<<P.nfblk, kBlock, 0, s>>>(P); }
 void launch_warm_density(const Ptrs &P, cudaStream_t s) { k_warm_density<<<P.nfblk, kBlock, 0, s>>>(P); }

@@ -45,6 +45,7 @@ struct SceneDev {
     int32_t fblk_first, fblk_count;   // fluid particle blocks of this scene
     int32_t bblk_first, bblk_count;   // boundary particle blocks
     int32_t cap_f, cap_b;             // neighbour list capacities
+    int32_t R;                        // stencil radius in cells: 1 (cell >= h), 2 (cell >= h/2)
     float cg_tol;
     int32_t cg_max;
 };
@@ -168,8 +169,8 @@ int32_t scan_tiles_for(int64_t n);
 // ------------------------------------------------------------------ fluid (sph_fluid.cu)
 void launch_step_begin(const Ptrs &P, cudaStream_t s);
 void launch_density_alpha(const Ptrs &P, cudaStream_t s);
-void launch_pass_a(const Ptrs &P, int solver, cudaStream_t s);
-void launch_pass_b(const Ptrs &P, int solver, int warm, cudaGraphConditionalHandle h,
+void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s);
+void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphConditionalHandle h,
                    int use_handle, cudaStream_t s);
 void launch_nonpressure(const Ptrs &P, cudaStream_t s);
 void launch_warm_density(const Ptrs &P, cudaStream_t s);

@@ -72,12 +72,13 @@ __global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving
     const int32_t cx = cell_coord(pb.x, sc.origin[0], sc.cell, sc.dims[0]);
     const int32_t cy = cell_coord(pb.y, sc.origin[1], sc.cell, sc.dims[1]);
     const int32_t cz = cell_coord(pb.z, sc.origin[2], sc.cell, sc.dims[2]);
-    const int32_t x0 = max(cx - 1, 0), x1 = min(cx + 1, sc.dims[0] - 1);
+    const int32_t R = sc.R;
+    const int32_t x0 = max(cx - R, 0), x1 = min(cx + R, sc.dims[0] - 1);
     float ws = 0.0f;
-    for (int32_t dz = -1; dz <= 1; ++dz) {
+    for (int32_t dz = -R; dz <= R; ++dz) {
         const int32_t z = cz + dz;
         if (z < 0 || z >= sc.dims[2]) continue;
-        for (int32_t dy = -1; dy <= 1; ++dy) {
+        for (int32_t dy = -R; dy <= R; ++dy) {
             const int32_t y = cy + dy;
             if (y < 0 || y >= sc.dims[1]) continue;
             const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);

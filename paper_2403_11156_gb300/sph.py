@@ -85,6 +85,20 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tuned", C.c_int32), ("from_cache", C.c_int32), ("gather_batch", C.c_int32),
+                ("cell_factor", C.c_float), ("n_trials", C.c_int32),
+                ("trial_cell_factor", C.c_float * 8), ("trial_batch", C.c_int32 * 8),
+                ("trial_ms", C.c_float * 8)]
+
+    def as_dict(self):
+        n = self.n_trials
+        return {"tuned": self.tuned, "from_cache": self.from_cache, "gather_batch": self.gather_batch,
+                "cell_factor": self.cell_factor,
+                "trials": [{"cell_factor": self.trial_cell_factor[k], "gather_batch": self.trial_batch[k],
+                            "ms_per_step": self.trial_ms[k]} for k in range(n)]}
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 64), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -130,13 +144,14 @@ def load():
     L.sph_destroy.argtypes = [vp]
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
     L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
+    L.sph_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.sph_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     L.sph_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.sph_mlp_train.argtypes = [vp, vp, C.c_int64, vp, vp, ip, ip, C.c_float, C.c_uint64, vp, vp, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train"):
+                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -230,11 +245,13 @@ def _make_desc(d, keep):
 class Context:
     """Owns one sph_ctx (one or several scenes).  Scene dicts come from ``scenes``."""
 
-    def __init__(self, scene_descs, stream=None, torch_allocator=True):
+    def __init__(self, scene_descs, stream=None, torch_allocator=True, autotune=False):
         L = load()
         if isinstance(scene_descs, dict):
             scene_descs = [scene_descs]
         self.descs = list(scene_descs)
+        if autotune:
+            self.descs = [dict(d, cell_size=-1.0) for d in self.descs]
         self._keep = []
         arr = (SceneDesc * len(self.descs))()
         for k, d in enumerate(self.descs):
@@ -350,6 +367,11 @@ class Context:
     def sph_set_mlp(self, params):
         a = np.ascontiguousarray(params, dtype=np.float32)
         _check(self.ctx, load().sph_set_mlp(self.ctx, _fptr(a), a.size))
+
+    def sph_get_tuning(self):
+        t = Tuning()
+        _check(self.ctx, load().sph_get_tuning(self.ctx, C.byref(t)))
+        return t.as_dict()
 
     def sph_launch_count(self):
         n = C.c_int64()

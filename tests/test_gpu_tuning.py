@@ -1,0 +1,50 @@
+"""Autotuner and the 125-cell stencil: with cells of h/2 (1 + 2^-8) the grid keys, the
+(key, id) order and the neighbour counts stay bit-exact against the oracle's contracts
+(the oracle's key function takes the cell size as a parameter), density and alpha stay
+within 1e-5; autotuning times four candidates, keeps the fastest and caches it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_11156_gb300 import scenes, sph
+
+from gpu_util import assert_rel, forced, gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def test_half_cell_stencil_parity():
+    d = forced(scenes.dam_break_small(seed=7, n=(9, 11, 13), box=0.4), 1, 2)
+    h = np.float32(4 * d["radius"])
+    d["cell_size"] = float(h * np.float32(0.501953125))
+    g = gpu_ctx(d)
+    g.sph_step(4e-4)
+    g.sph_synchronize(raise_on_error=False)
+    x = d["fluid_x"]
+    keys = oracle.cell_keys(x, d["domain_min"], d["domain_max"], d["cell_size"])
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_CELL_KEY), keys)
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_SORTED_ID), oracle.sort_order(keys))
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_NN_FLUID), oracle.neighbor_counts_brute(x, x, h, True))
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_NN_BOUNDARY),
+                                  oracle.neighbor_counts_brute(x, d["boundary_x"], h, False))
+    o = oracle.Scene(d)
+    o.step(4e-4)
+    assert_rel(g.sph_read_field(sph.FIELD_RHO), o.get(oracle.RHO), 1e-5, what="rho")
+    assert_rel(g.sph_read_field(sph.FIELD_ALPHA), o.get(oracle.ALPHA), 1e-5, what="alpha")
+    assert_rel(g.sph_read_field(sph.FIELD_PSI), o.get(oracle.PSI), 1e-5, what="psi")
+
+
+def test_autotune_picks_fastest_and_caches():
+    d = scenes.dam_break_small(seed=9)
+    g = gpu_ctx(d, autotune=True)
+    t = g.sph_get_tuning()
+    assert t["tuned"] == 1 and t["from_cache"] == 0 and len(t["trials"]) == 4
+    best = min(t["trials"], key=lambda r: r["ms_per_step"])
+    assert t["gather_batch"] == best["gather_batch"] and t["cell_factor"] == pytest.approx(best["cell_factor"])
+    g.sph_steps(20, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    st = g.sph_get_stats()
+    assert st["dens_err"] <= 1e-3 and st["flags"] == 0
+    g2 = gpu_ctx(d, autotune=True)
+    t2 = g2.sph_get_tuning()
+    assert t2["from_cache"] == 1 and t2["gather_batch"] == t["gather_batch"]
