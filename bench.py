@@ -141,6 +141,42 @@ def learned_vs_plain():
     return out
 
 
+def batched_throughput(steps=30):
+    """64 independent dam breaks (20k-200k particles, log-uniform, seed 5) in one context:
+    every kernel of a step covers all scenes in one launch.  Returns particle-steps/s of
+    the batch and of the same scenes stepped one at a time (8 of them, scaled)."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    ds = scenes.batch_dam_break()
+    nf = sum(len(d["fluid_x"]) for d in ds)
+    stream = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with sph.Context(ds, stream=stream) as g:
+        g.sph_steps(5, 0.0)
+        g.sph_synchronize(raise_on_error=False)
+        a.record(stream)
+        g.sph_steps(steps, 0.0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        st = [g.sph_get_stats(k) for k in range(len(ds))]
+    single_ms, single_n = 0.0, 0
+    for k in range(0, len(ds), 8):
+        with sph.Context(ds[k], stream=stream) as g:
+            g.sph_steps(5, 0.0)
+            g.sph_synchronize(raise_on_error=False)
+            a.record(stream)
+            g.sph_steps(steps, 0.0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            single_ms += a.elapsed_time(b) / steps
+            single_n += len(ds[k]["fluid_x"])
+    return {"scenes": len(ds), "fluid_particles": nf, "ms_per_step": ms,
+            "particle_steps_per_s": nf / (ms / 1000.0),
+            "one_at_a_time_particle_steps_per_s": single_n / (single_ms / 1000.0),
+            "density_iters_range": [min(x["dens_iters"] for x in st), max(x["dens_iters"] for x in st)]}
+
+
 def reference_sample():
     from paper_2403_11156_gb300 import scenes
     # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
@@ -186,6 +222,7 @@ def main():
     ap.add_argument("--timing-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default 27-cell stencil and gather batch instead of autotuning")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batch measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-vs-plain warm-start comparison")
     args = ap.parse_args()
@@ -296,6 +333,9 @@ def main():
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_vs_plain()
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_throughput()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -317,6 +357,7 @@ def main():
                    "autotune": tuning},
         "clocks": clocks.summary(), "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
+        "batched_64_scenes": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -284,6 +284,14 @@ sph_status sph_mlp_train(const float *features, const float *labels, int64_t n, 
                          float *adam_state, int32_t epochs, int32_t batch, float lr, uint64_t seed,
                          float *loss_history, int32_t *error, void *stream);
 
+/* Device trace for profiling graph replays: with capacity > 0 every kernel's first thread
+ * records (globaltimer_ns << 8 | kernel id) in a device ring of that many entries (the
+ * library allocates it; 0 turns tracing off and frees it).  sph_read_trace copies up to
+ * cap entries to host memory, returns the count recorded in *n and, with reset != 0,
+ * restarts recording.  Kernel ids are the SPH_KID_* values of the library's kernels. */
+sph_status sph_set_trace(sph_ctx *ctx, int32_t capacity);
+sph_status sph_read_trace(sph_ctx *ctx, uint64_t *out, int32_t cap, int32_t *n, int32_t reset);
+
 /* Kernel launches enqueued since creation (counted on the device for graph replays). */
 sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -67,6 +68,8 @@ struct sph_ctx {
     int64_t host_launches = 0;
 
     std::vector<int32_t> reported_flags;
+    unsigned long long *trace = nullptr; // device trace ring (cudaMalloc, owned)
+    int32_t trace_cap = 0;
     int batch = 4;                       // neighbours in flight per thread in the Jacobi passes
     sph_tuning tuning{};
     uint32_t *h_flag = nullptr;          // pinned word for eager loop control
@@ -1228,6 +1231,41 @@ sph_status sph_set_mlp(sph_ctx *c, const float *params, int64_t n)
     return SPH_OK;
 }
 
+sph_status sph_set_trace(sph_ctx *c, int32_t capacity)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (capacity < 0 || capacity > (1 << 26)) return fail(c, SPH_EINVAL, "trace capacity out of range");
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned long long *nt = nullptr;
+    if (capacity > 0) CK(cudaMalloc(&nt, sizeof(unsigned long long) * capacity));
+    const uint32_t counts[2] = {0u, (uint32_t)capacity};
+    CK(cudaMemcpy(&c->P.ctl->trace, &nt, sizeof nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&c->P.ctl->trace_n, counts, sizeof counts, cudaMemcpyHostToDevice));
+    if (c->trace) cudaFree(c->trace);
+    c->trace = nt;
+    c->trace_cap = capacity;
+    return SPH_OK;
+}
+
+sph_status sph_read_trace(sph_ctx *c, uint64_t *out, int32_t cap, int32_t *n, int32_t reset)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    uint32_t cnt = 0;
+    CK(cudaMemcpy(&cnt, &c->P.ctl->trace_n, sizeof cnt, cudaMemcpyDeviceToHost));
+    const uint32_t avail = std::min<uint32_t>(cnt, (uint32_t)c->trace_cap);
+    if (out && c->trace && cap > 0)
+        CK(cudaMemcpy(out, c->trace, sizeof(uint64_t) * std::min<uint32_t>(avail, (uint32_t)cap), cudaMemcpyDeviceToHost));
+    if (n) *n = (int32_t)cnt;
+    if (reset) {
+        const uint32_t zero = 0;
+        CK(cudaMemcpy(&c->P.ctl->trace_n, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    }
+    return SPH_OK;
+}
+
 sph_status sph_launch_count(sph_ctx *c, int64_t *out)
 {
     sph_status st = check_ctx(c);
@@ -1277,6 +1315,7 @@ void sph_destroy(sph_ctx *c)
         else cudaFree(a.p);
     }
     if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->trace) cudaFree(c->trace);
     if (c->cap0) cudaStreamDestroy(c->cap0);
     if (c->cap1) cudaStreamDestroy(c->cap1);
     delete c;

@@ -15,12 +15,6 @@ namespace sph {
 
 namespace {
 
-__device__ __forceinline__ void count_launch(Control *ctl)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
-}
-
 // Cubic spline (Sec. 3.2 with h = 4r, Sec. 5): W = sigma w(q), grad W = kgrad g(q) x/|x|.
 __device__ __forceinline__ float spline_w(float q)
 {
@@ -102,7 +96,7 @@ __device__ double block_sum(double v, double *sh)
 // Step begin: per-scene counters and the step size.
 __global__ void k_step_begin(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_STEP_BEGIN);
     int s = threadIdx.x + blockIdx.x * blockDim.x;
     if (s == 0) {
         P.ctl->passb_counter = 0;
@@ -168,7 +162,7 @@ __device__ __forceinline__ void for_range(const float4 *__restrict__ pos, uint32
 // gate of the divergence warm start (D rho/Dt with the velocities at step start).
 __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_DENSITY);
     BlockCtx c = fluid_ctx(P);
     const SceneDev &sc = *c.sc;
     int nn_f = 0, nn_b = 0;
@@ -322,7 +316,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, (KID_PASS_A0 + S));
     BlockCtx c = fluid_ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
@@ -383,7 +377,7 @@ template <int S, int WARM, int B>
 __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
 {
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, (WARM ? KID_PASS_B0W + S : KID_PASS_B0 + S));
     BlockCtx c = fluid_ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
@@ -459,7 +453,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
 // velocity array and clears the density-solve stiffness sum.
 __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_NONP);
     BlockCtx c = fluid_ctx(P);
     if (!c.valid) return;
     const SceneDev &sc = *c.sc;
@@ -512,7 +506,7 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 // (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.
 __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_WARM);
     BlockCtx c = fluid_ctx(P);
     if (!c.valid) return;
     const SceneDev &sc = *c.sc;
@@ -548,7 +542,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
 // back in grid order as the next step's canonical state, with the warm-start memory.
 __global__ void __launch_bounds__(kBlock) k_advect(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_ADVECT);
     BlockCtx c = fluid_ctx(P);
     float v2 = 0.0f;
     bool bad = false;
@@ -583,7 +577,7 @@ __global__ void __launch_bounds__(kBlock) k_advect(Ptrs P)
 // quaternion; weak coupling: bodies move only between fluid steps, Sec. 2.2 / 6).
 __global__ void k_step_end(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_STEP_END);
     int t = threadIdx.x;
     for (int s = t; s < P.nscenes; s += blockDim.x) {
         const SceneDev &sc = P.scenes[s];
@@ -648,7 +642,7 @@ __global__ void k_step_end(Ptrs P)
 
 __global__ void k_set_dt(Control *ctl, float dt)
 {
-    count_launch(ctl);
+    kernel_enter(ctl, KID_SET_DT);
     ctl->dt_override = dt;
 }
 

@@ -8,12 +8,6 @@ namespace sph {
 
 namespace {
 
-__device__ __forceinline__ void count_launch(Control *ctl)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
-}
-
 __device__ __forceinline__ uint32_t cell_of(const SceneDev &sc, float4 p)
 {
     int32_t ix = cell_coord(p.x, sc.origin[0], sc.cell, sc.dims[0]);
@@ -26,7 +20,7 @@ __device__ __forceinline__ uint32_t cell_of(const SceneDev &sc, float4 p)
 template <int WHAT>
 __global__ void __launch_bounds__(kBlock) k_key_hist(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, (WHAT == SORT_FLUID ? KID_KEY_HIST_F : KID_KEY_HIST_B));
     const int32_t *tab = WHAT == SORT_FLUID ? P.fblk_scene : P.bblk_scene;
     const SceneDev &sc = P.scenes[tab[blockIdx.x]];
     const int32_t first = WHAT == SORT_FLUID ? sc.fblk_first : sc.bblk_first;
@@ -47,7 +41,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(Ptrs P)
 template <int WHAT>
 __global__ void __launch_bounds__(kBlock) k_scatter(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, (WHAT == SORT_FLUID ? KID_SCATTER_F : KID_SCATTER_B));
     const int32_t *tab = WHAT == SORT_FLUID ? P.fblk_scene : P.bblk_scene;
     const SceneDev &sc = P.scenes[tab[blockIdx.x]];
     const int32_t first = WHAT == SORT_FLUID ? sc.fblk_first : sc.bblk_first;
@@ -70,7 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(Ptrs P)
 template <int WHAT>
 __global__ void __launch_bounds__(kBlock) k_rank_gather(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, (WHAT == SORT_FLUID ? KID_RANK_F : KID_RANK_B));
     const int32_t *tab = WHAT == SORT_FLUID ? P.fblk_scene : P.bblk_scene;
     const SceneDev &sc = P.scenes[tab[blockIdx.x]];
     const int32_t first = WHAT == SORT_FLUID ? sc.fblk_first : sc.bblk_first;
@@ -131,7 +125,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t
     __shared__ uint32_t s_epoch;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_prefix;
-    count_launch(ctl);
+    kernel_enter(ctl, KID_SCAN);
     if (threadIdx.x == 0) {
         s_tile = atomicAdd(&ctl->scan_tile_counter, 1);
         s_epoch = *reinterpret_cast<volatile uint32_t *>(&ctl->scan_epoch);

@@ -94,7 +94,59 @@ struct Control {
     uint32_t scan_epoch;
     int32_t error;                    // bounded-wait failures
     int32_t have_mlp;                 // warm-start network loaded
+    uint32_t trace_n, trace_cap;      // device trace: stamps written / capacity
+    unsigned long long *trace;        // (globaltimer << 8 | kernel id) per launch, or null
 };
+
+// Kernel identifiers of the device trace.
+enum KernelId : uint32_t {
+    KID_STEP_BEGIN = 1,
+    KID_KEY_HIST_F = 2,
+    KID_KEY_HIST_B = 3,
+    KID_SCAN = 4,
+    KID_SCATTER_F = 5,
+    KID_SCATTER_B = 6,
+    KID_RANK_F = 7,
+    KID_RANK_B = 8,
+    KID_DENSITY = 9,
+    KID_PASS_A0 = 10,
+    KID_PASS_A1 = 11,
+    KID_PASS_B0 = 12,
+    KID_PASS_B1 = 13,
+    KID_PASS_B0W = 14,
+    KID_PASS_B1W = 15,
+    KID_NONP = 16,
+    KID_WARM = 17,
+    KID_ADVECT = 18,
+    KID_STEP_END = 19,
+    KID_SET_DT = 20,
+    KID_BUPDATE = 21,
+    KID_PSI = 22,
+    KID_BFORCE = 23,
+    KID_BREDUCE = 24,
+    KID_CG_INIT = 25,
+    KID_CG_AP = 26,
+    KID_CG_XR = 27,
+    KID_CG_P = 28,
+    KID_MLP_WARM = 29
+};
+
+// First thread of every kernel: count the launch and, when tracing, stamp its start.
+__device__ __forceinline__ void kernel_enter(Control *ctl, uint32_t id)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
+        unsigned long long *tr = ctl->trace;
+        if (tr) {
+            const uint32_t k = atomicAdd(&ctl->trace_n, 1u);
+            if (k < ctl->trace_cap) {
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                tr[k] = (t << 8) | id;
+            }
+        }
+    }
+}
 
 struct Ptrs {
     const SceneDev *scenes;

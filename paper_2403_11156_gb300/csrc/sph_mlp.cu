@@ -50,12 +50,6 @@ constexpr uint32_t kSmRequest = 72 * 1024;
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kWaitLimit = 1u << 20;
 
-__device__ __forceinline__ void count_launch(Control *ctl)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
-}
-
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
 __device__ __forceinline__ uint32_t pack2(float a, float b)
@@ -187,7 +181,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ w
 __global__ void __launch_bounds__(128) k_mlp_warm(Ptrs P)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_MLP_WARM);
     const int32_t s = P.fblk_scene[blockIdx.x];
     const SceneDev &sc = P.scenes[s];
     if (sc.warm != 2 || !P.ctl->have_mlp) return;  // uniform per block, before any allocation

@@ -13,12 +13,6 @@ namespace sph {
 
 namespace {
 
-__device__ __forceinline__ void count_launch(Control *ctl)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
-}
-
 __device__ __forceinline__ float spline_w(float q)
 {
     if (q <= 0.5f) return fmaf(6.0f * q, q * q, fmaf(-6.0f * q, q, 1.0f));
@@ -38,7 +32,7 @@ __device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
 // Boundary particles of moving bodies follow their body (original order).
 __global__ void __launch_bounds__(kBlock) k_boundary_update(Ptrs P)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_BUPDATE);
     const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
     if (!sc.has_moving) return;
     int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
@@ -62,7 +56,7 @@ __global__ void __launch_bounds__(kBlock) k_boundary_update(Ptrs P)
 // Psi_b = rho0 / (sigma (1 + sum_k w(q_bk)))  (grid order; stored in bpos_s.w)
 __global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving)
 {
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_PSI);
     const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
     if (only_moving && !sc.has_moving) return;
     int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
@@ -113,7 +107,7 @@ __device__ double block_sum_d(double v, double *sh)
 __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_BFORCE);
     const SceneDev &sc = P.scenes[P.fblk_scene[blockIdx.x]];
     if (sc.nbody == 0) return;
     int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
@@ -172,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
 __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
 {
     __shared__ double sh[8];
+    kernel_enter(P.ctl, KID_BREDUCE);
     const int body = blockIdx.x / 6, a = blockIdx.x % 6;
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];

@@ -14,12 +14,6 @@ namespace sph {
 
 namespace {
 
-__device__ __forceinline__ void count_launch(Control *ctl)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->launches), 1ull);
-}
-
 __device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
 {
     if (!(r2 > 0.0f)) return 0.0f;
@@ -141,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_CG_INIT);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
@@ -173,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_ap(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_CG_AP);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
@@ -195,7 +189,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_CG_XR);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
@@ -226,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
 __global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
 {
     __shared__ int s_last;
-    count_launch(P.ctl);
+    kernel_enter(P.ctl, KID_CG_P);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;

@@ -39,6 +39,14 @@ FIELD_LAYOUT = {
 }
 
 
+KERNEL_IDS = {i + 1: n for i, n in enumerate([
+    "step_begin", "key_hist_fluid", "key_hist_boundary", "scan", "scatter_fluid", "scatter_boundary",
+    "rank_gather_fluid", "rank_gather_boundary", "density_alpha", "div_pass_a", "dens_pass_a",
+    "div_pass_b", "dens_pass_b", "div_warm_pass_b", "dens_warm_pass_b", "nonpressure", "warm_density",
+    "advect", "step_end", "set_dt", "boundary_update", "boundary_psi", "body_force", "body_reduce",
+    "cg_init", "cg_ap", "cg_xr", "cg_p", "mlp_warm"])}
+
+
 class SphError(RuntimeError):
     def __init__(self, status, msg):
         self.status = status
@@ -145,13 +153,16 @@ def load():
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
     L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
     L.sph_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.sph_set_trace.argtypes = [vp, ip]
+    L.sph_read_trace.argtypes = [vp, vp, ip, C.POINTER(C.c_int32), ip]
     L.sph_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     L.sph_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.sph_mlp_train.argtypes = [vp, vp, C.c_int64, vp, vp, ip, ip, C.c_float, C.c_uint64, vp, vp, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning"):
+                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
+                 "sph_read_trace"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -372,6 +383,18 @@ class Context:
         t = Tuning()
         _check(self.ctx, load().sph_get_tuning(self.ctx, C.byref(t)))
         return t.as_dict()
+
+    def sph_set_trace(self, capacity):
+        _check(self.ctx, load().sph_set_trace(self.ctx, int(capacity)))
+
+    def sph_read_trace(self, cap=1 << 20, reset=True):
+        """Returns (kernel names, start times in ns) of the traced launches in order."""
+        buf = np.zeros(cap, dtype=np.uint64)
+        n = C.c_int32()
+        _check(self.ctx, load().sph_read_trace(self.ctx, buf.ctypes.data, cap, C.byref(n), int(reset)))
+        k = min(n.value, cap)
+        raw = buf[:k]
+        return [KERNEL_IDS.get(int(r & 0xFF), "?") for r in raw], (raw >> np.uint64(8)).astype(np.int64)
 
     def sph_launch_count(self):
         n = C.c_int64()

@@ -59,3 +59,16 @@ def test_twenty_steps_invariants(c2):
     x, v, rho, p = g.sph_read_state()
     assert len(x) == 1200500 and np.all(np.isfinite(x)) and np.all(np.isfinite(v))
     assert np.all(x >= -0.01) and np.all(x[:, 0] <= 2.01)
+
+
+def test_batch_of_64_scenes():
+    # 64 dam breaks of 20k-200k particles (5.07M total) in one context
+    ds = scenes.batch_dam_break()
+    g = gpu_ctx(ds)
+    g.sph_steps(10, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    for k in (0, 17, 63):
+        st = g.sph_get_stats(k)
+        assert st["steps"] == 10 and st["flags"] == 0 and st["dens_err"] <= 1e-3
+        x, v, _, _ = g.sph_read_state(k)
+        assert len(x) == len(ds[k]["fluid_x"]) and np.all(np.isfinite(x))
