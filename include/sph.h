@@ -99,6 +99,14 @@ typedef struct sph_scene_desc {
     int32_t max_boundary_neighbors; /* 0 = 64                                         */
     float cg_tol;                 /* relative residual of the implicit viscosity CG   */
     int32_t cg_max_iter;
+    int32_t lanes_per_particle;   /* threads per fluid particle in the neighbour      */
+                                  /* sweeps: 1, 2 or 4; 0 = by size (4 up to 77,824   */
+                                  /* fluid particles in the context, 2 up to twice    */
+                                  /* that, else 1).  Each lane keeps its own          */
+                                  /* neighbour sub-list of ceil(1.5 cap / lanes)      */
+                                  /* entries (cap for 1 lane); 4 lanes need           */
+                                  /* max_*_neighbors <= 680.  A batch uses the largest */
+                                  /* value given by its scenes.                       */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64
@@ -216,12 +224,14 @@ sph_status sph_read_bodies(sph_ctx *ctx, int32_t scene, double *out);
 sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
 
 /* Autotuning.  A scene created with cell_size < 0 lets sph_create choose its grid cell
- * size (h (1 + 2^-8), 27-cell stencil, or h/2 (1 + 2^-8), 125-cell stencil) and the
- * number of neighbours each thread keeps in flight in the Jacobi passes (4 or 8) by
- * timing a few CUDA-graph steps of every candidate on temporary contexts; the choice is
- * cached per process for the same device and workload size (log2 of the fluid count,
- * scene count, bodies, viscosity mode).  Neighbour sets do not depend on the choice;
- * the summation order, and so the last bits of FP32 results, may. */
+ * size (h (1 + 2^-8), 27-cell stencil, or h/2 (1 + 2^-8), 125-cell stencil), the threads
+ * per particle of the neighbour sweeps (1, 2 or 4; kept fixed when lanes_per_particle is
+ * set) and, with one thread per particle, the number of neighbours each thread keeps in
+ * flight in the Jacobi passes (4 or 8) by timing a few CUDA-graph steps of every
+ * candidate on temporary contexts; the choice is cached per process for the same device
+ * and workload size (log2 of the fluid count, scene count, bodies, viscosity mode,
+ * lanes_per_particle).  Neighbour sets do not depend on the choice; the summation order,
+ * and so the last bits of FP32 results, may. */
 typedef struct sph_tuning {
     int32_t tuned;            /* 1 if this context was autotuned                     */
     int32_t from_cache;       /* the choice came from the per-process cache          */
@@ -231,6 +241,8 @@ typedef struct sph_tuning {
     float trial_cell_factor[8];
     int32_t trial_batch[8];
     float trial_ms[8];        /* mean milliseconds per step of each candidate        */
+    int32_t lanes;            /* chosen threads per particle                         */
+    int32_t trial_lanes[8];
 } sph_tuning;
 sph_status sph_get_tuning(sph_ctx *ctx, sph_tuning *out);
 

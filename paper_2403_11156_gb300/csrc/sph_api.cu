@@ -20,6 +20,16 @@ namespace {
 
 constexpr int kDefaultCapF = 96;
 constexpr int kDefaultCapB = 64;
+constexpr int kDefaultLanes = 1;
+constexpr int64_t kAutoLaneThreads = 152 * 2048;  // resident threads of a full GB300
+
+// Capacity of one lane's sub-list: with T > 1 lanes a particle's neighbours are dealt to
+// the lanes by candidate index, so each sub-list gets half again its even share.
+int lane_cap(int cap, int lanes)
+{
+    return lanes == 1 ? cap : std::min(cap, (3 * cap + 2 * lanes - 1) / (2 * lanes));
+}
+int lanes_of(const sph_scene_desc &d) { return d.lanes_per_particle > 0 ? d.lanes_per_particle : kDefaultLanes; }
 constexpr double kPi = 3.14159265358979323846;
 
 struct Alloc {
@@ -46,7 +56,7 @@ struct sph_ctx {
 
     int nscenes = 0;
     std::vector<SceneDev> scenes;        // host copies
-    std::vector<int32_t> fblk_scene, bblk_scene;
+    std::vector<int32_t> fblk_scene, bblk_scene, tblk_scene;
     std::vector<int32_t> nbody_scene;
     int max_bodies = 0;
     bool any_moving = false, any_div = false, any_warm_div = false, any_warm = false,
@@ -160,6 +170,16 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.warm_start < 0 || d.warm_start > 2) return bad("warm_start");
     if (d.max_fluid_neighbors < 0 || d.max_fluid_neighbors > 1024) return bad("max_fluid_neighbors");
     if (d.max_boundary_neighbors < 0 || d.max_boundary_neighbors > 1024) return bad("max_boundary_neighbors");
+    if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
+        d.lanes_per_particle != 4)
+        return bad("lanes_per_particle (0, 1, 2 or 4)");
+    {
+        const int L = lanes_of(d);
+        const int cf = d.max_fluid_neighbors > 0 ? d.max_fluid_neighbors : kDefaultCapF;
+        const int cb = d.max_boundary_neighbors > 0 ? d.max_boundary_neighbors : kDefaultCapB;
+        if (L > 1 && (lane_cap(cf, L) >= (1 << (32 / L)) || lane_cap(cb, L) >= (1 << (32 / L))))
+            return bad("max_*_neighbors too large for 4 lanes per particle (at most 680)");
+    }
     if (d.cell_size > 0.0f && !(d.cell_size >= half_cell(d.radius))) return bad("cell_size below h/2 (1 + 2^-8)");
     if (!std::isfinite(d.cell_size)) return bad("cell_size not finite");
     if (d.n_bodies < 0 || d.n_bodies > SPH_MAX_BODIES) return bad("n_bodies out of range");
@@ -217,8 +237,8 @@ __global__ void k_read_fluid(Ptrs P, int scene, int field, void *out)
     case SPH_FIELD_ALPHA: ((float *)out)[P.id_s[i]] = P.alpha[i]; break;
     case SPH_FIELD_KAPPA: ((float *)out)[P.id_s[i]] = P.ksum[i]; break;
     case SPH_FIELD_KAPPA_V: ((float *)out)[P.id_s[i]] = P.kvsum[i]; break;
-    case SPH_FIELD_NN_FLUID: ((int32_t *)out)[P.id_s[i]] = P.nnf[i]; break;
-    case SPH_FIELD_NN_BOUNDARY: ((int32_t *)out)[P.id_s[i]] = P.nnb[i]; break;
+    case SPH_FIELD_NN_FLUID: ((int32_t *)out)[P.id_s[i]] = nn_total(P.nnf[i], P.lanes); break;
+    case SPH_FIELD_NN_BOUNDARY: ((int32_t *)out)[P.id_s[i]] = nn_total(P.nnb[i], P.lanes); break;
     case SPH_FIELD_V_DIV: {
         float4 v = P.vel_s[i];
         float *o = (float *)out + 3 * P.id_s[i];
@@ -535,8 +555,25 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     c->nscenes = n;
     c->scenes.resize(n);
     int64_t NF = 0, NB = 0, NC = 0;
-    int32_t nfblk = 0, nbblk = 0, nbodies = 0;
-    int cap_f = 0, cap_b = 0;
+    int32_t nfblk = 0, nbblk = 0, ntblk = 0, nbodies = 0;
+    int lcap_f = 0, lcap_b = 0;
+    // threads per particle in the neighbour sweeps: one value for the whole context, the
+    // largest one given, else by size: enough threads to fill every SM (4 lanes below
+    // 152 x 2048 / 4 particles, 2 below twice that), as far as the list capacities allow
+    int lanes = 0;
+    for (int s = 0; s < n; ++s) lanes = std::max(lanes, (int)descs[s].lanes_per_particle);
+    if (lanes == 0) {
+        int64_t nf = 0;
+        int cap = 0;
+        for (int s = 0; s < n; ++s) {
+            nf += descs[s].n_fluid;
+            cap = std::max(cap, descs[s].max_fluid_neighbors > 0 ? descs[s].max_fluid_neighbors : kDefaultCapF);
+            cap = std::max(cap, descs[s].max_boundary_neighbors > 0 ? descs[s].max_boundary_neighbors : kDefaultCapB);
+        }
+        const int64_t fill = kAutoLaneThreads;
+        lanes = nf * 4 <= fill ? 4 : (nf * 2 <= fill ? 2 : 1);
+        while (lanes > 1 && lane_cap(cap, lanes) >= (1 << (32 / lanes))) lanes /= 2;
+    }
     for (int s = 0; s < n; ++s) {
         const sph_scene_desc &d = descs[s];
         SceneDev &q = c->scenes[s];
@@ -588,19 +625,27 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.fblk_count = (int32_t)((d.n_fluid + kBlock - 1) / kBlock);
         q.bblk_first = nbblk;
         q.bblk_count = (int32_t)((d.n_boundary + kBlock - 1) / kBlock);
+        q.tblk_first = ntblk;
+        q.tblk_count = (int32_t)((d.n_fluid * lanes + kBlock - 1) / kBlock);
         q.cap_f = d.max_fluid_neighbors > 0 ? d.max_fluid_neighbors : kDefaultCapF;
         q.cap_b = d.max_boundary_neighbors > 0 ? d.max_boundary_neighbors : kDefaultCapB;
+        q.lcap_f = lane_cap(q.cap_f, lanes);
+        q.lcap_b = lane_cap(q.cap_b, lanes);
         q.cg_tol = d.cg_tol > 0.0f ? d.cg_tol : 1e-4f;
         q.cg_max = d.cg_max_iter > 0 ? d.cg_max_iter : 500;
-        cap_f = std::max(cap_f, q.cap_f);
-        cap_b = std::max(cap_b, q.cap_b);
+        if (lanes > 1 && (q.lcap_f >= (1 << (32 / lanes)) || q.lcap_b >= (1 << (32 / lanes))))
+            return bail(fail(c, SPH_EINVAL, "scene %d: max_*_neighbors too large for %d lanes per particle", s, lanes));
+        lcap_f = std::max(lcap_f, q.lcap_f);
+        lcap_b = std::max(lcap_b, q.lcap_b);
         for (int k = 0; k < q.fblk_count; ++k) c->fblk_scene.push_back(s);
         for (int k = 0; k < q.bblk_count; ++k) c->bblk_scene.push_back(s);
+        for (int k = 0; k < q.tblk_count; ++k) c->tblk_scene.push_back(s);
         NF += d.n_fluid;
         NB += d.n_boundary;
         NC += nc;
         nfblk += q.fblk_count;
         nbblk += q.bblk_count;
+        ntblk += q.tblk_count;
         nbodies += d.n_bodies;
         c->max_bodies = std::max(c->max_bodies, (int)d.n_bodies);
         c->any_moving |= d.n_bodies > 0;
@@ -611,11 +656,13 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         c->any_learned |= d.warm_start == 2;
         c->any_implicit |= d.viscosity_mode == 3;
     }
-    if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * cap_f > 4.0e10)
+    if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * lanes * lcap_f > 4.0e10)
         return bail(fail(c, SPH_EINVAL, "context too large"));
     Ptrs &P = c->P;
     P.nfblk = nfblk;
     P.nbblk = nbblk;
+    P.ntblk = ntblk;
+    P.lanes = lanes;
     P.nscenes = n;
     P.nbodies_total = nbodies;
     P.NF = NF;
@@ -629,15 +676,16 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, st, n);
     ok &= dalloc(c, P.ctl, 1);
     ok &= dalloc(c, P.bodies, std::max(nbodies, 1));
-    int32_t *fbs = nullptr, *bbs = nullptr;
+    int32_t *fbs = nullptr, *bbs = nullptr, *tbs = nullptr;
     ok &= dalloc(c, fbs, std::max(nfblk, 1));
     ok &= dalloc(c, bbs, std::max(nbblk, 1));
+    ok &= dalloc(c, tbs, std::max(ntblk, 1));
     ok &= dalloc(c, P.pos_s, NF) && dalloc(c, P.vel_s, NF) && dalloc(c, P.pos_c, NF) && dalloc(c, P.vel_c, NF);
     ok &= dalloc(c, P.kprev_c, NF) && dalloc(c, P.kvprev_c, NF) && dalloc(c, P.kprev_s, NF) &&
           dalloc(c, P.kvprev_s, NF);
     ok &= dalloc(c, P.ksum, NF) && dalloc(c, P.kvsum, NF) && dalloc(c, P.alpha, NF) && dalloc(c, P.k0, NF);
     ok &= dalloc(c, P.id_c, NF) && dalloc(c, P.id_s, NF) && dalloc(c, P.nnf, NF) && dalloc(c, P.nnb, NF);
-    ok &= dalloc(c, P.nbr, (size_t)NF * cap_f) && dalloc(c, P.bnbr, (size_t)NF * cap_b);
+    ok &= dalloc(c, P.nbr, (size_t)NF * lanes * lcap_f) && dalloc(c, P.bnbr, (size_t)NF * lanes * lcap_b);
     ok &= dalloc(c, P.feat, (size_t)NF * 4);
     ok &= dalloc(c, P.cell_count, NC) && dalloc(c, P.cell_start, NC + 1);
     ok &= dalloc(c, P.key_tmp, NF) && dalloc(c, P.slot_tmp, NF) && dalloc(c, P.sid_tmp, NF) &&
@@ -649,11 +697,11 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, P.bcell_count, NC) && dalloc(c, P.bcell_start, NC + 1);
     ok &= dalloc(c, P.bkey_tmp, NBa) && dalloc(c, P.bslot_tmp, NBa) && dalloc(c, P.bsid_tmp, NBa) &&
           dalloc(c, P.bsrc_tmp, NBa) && dalloc(c, P.bcell_tmp, NBa);
-    ok &= dalloc(c, P.partial, std::max(nfblk, 1));
-    ok &= dalloc(c, P.body_partial, (size_t)std::max(nfblk, 1) * std::max(nbodies, 1) * 6);
+    ok &= dalloc(c, P.partial, std::max(ntblk, 1));
+    ok &= dalloc(c, P.body_partial, (size_t)std::max(ntblk, 1) * std::max(nbodies, 1) * 6);
     if (c->any_implicit) {
         ok &= dalloc(c, P.cg_r, NF) && dalloc(c, P.cg_p, NF) && dalloc(c, P.cg_ap, NF);
-        ok &= dalloc(c, P.cg_dots, 2 * (size_t)std::max(nfblk, 1));
+        ok &= dalloc(c, P.cg_dots, 2 * (size_t)std::max(std::max(nfblk, ntblk), 1));
     }
     ok &= dalloc(c, P.mlp_w, SPH_MLP_PARAMS);
     P.scan_tiles = scan_tiles_for(NC);
@@ -663,6 +711,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     P.st = st;
     P.fblk_scene = fbs;
     P.bblk_scene = bbs;
+    P.tblk_scene = tbs;
     if (cudaMallocHost(&c->h_flag, sizeof(uint32_t)) != cudaSuccess)
         return bail(fail(c, SPH_ENOMEM, "pinned allocation failed"));
 
@@ -775,6 +824,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= up(P.ctl, &hctl, sizeof hctl);
     ok &= up(P.bodies, hb.data(), sizeof(BodyDev) * hb.size());
     ok &= up(fbs, c->fblk_scene.data(), sizeof(int32_t) * std::max(nfblk, 0));
+    ok &= up(tbs, c->tblk_scene.data(), sizeof(int32_t) * std::max(ntblk, 0));
     if (nbblk) ok &= up(bbs, c->bblk_scene.data(), sizeof(int32_t) * nbblk);
     ok &= cudaMemsetAsync(P.cell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.bcell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
@@ -825,8 +875,8 @@ std::string tune_key(const sph_scene_desc *d, int32_t n)
     int bucket = 0;
     while ((int64_t)1 << (bucket + 1) <= nf) ++bucket;
     char buf[512];
-    snprintf(buf, sizeof buf, "%s|fluid2^%d|scenes%d|bodies%d|visc%d", name, bucket, n, d[0].n_bodies,
-             d[0].viscosity_mode);
+    snprintf(buf, sizeof buf, "%s|fluid2^%d|scenes%d|bodies%d|visc%d|lanes%d", name, bucket, n, d[0].n_bodies,
+             d[0].viscosity_mode, d[0].lanes_per_particle);
     return buf;
 }
 
@@ -856,8 +906,9 @@ sph_status time_config(const std::vector<sph_scene_desc> &descs, const sph_alloc
     return st;
 }
 
-// Scenes with cell_size < 0: pick the cell size (27- or 125-cell stencil) and the gather
-// batch by timing each candidate, cache the choice, and build the context with it.
+// Scenes with cell_size < 0: pick the cell size (27- or 125-cell stencil), the threads
+// per particle of the sweeps and the gather batch by timing each candidate, cache the
+// choice, and build the context with it.
 sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_allocator *alloc, void *stream,
                         sph_ctx **out)
 {
@@ -873,26 +924,42 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
             cached = true;
         }
     }
+    // lanes given by the caller stay fixed; 4 lanes need capacities of at most 680
+    int fixed_lanes = 0, max_cap = 0;
+    for (int s = 0; s < n; ++s) {
+        fixed_lanes = std::max(fixed_lanes, (int)descs[s].lanes_per_particle);
+        max_cap = std::max(max_cap, descs[s].max_fluid_neighbors > 0 ? descs[s].max_fluid_neighbors : kDefaultCapF);
+        max_cap = std::max(max_cap, descs[s].max_boundary_neighbors > 0 ? descs[s].max_boundary_neighbors : kDefaultCapB);
+    }
+    auto set_trial = [&](float factor, int lanes) {
+        for (int s = 0; s < n; ++s) {
+            trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * factor : descs[s].cell_size;
+            trial[s].lanes_per_particle = lanes;
+        }
+    };
     if (!cached) {
         const float factors[2] = {1.00390625f, 0.501953125f};
-        const int batches[2] = {4, 8};
+        const int lanes_c[4] = {1, 1, 2, 4}, batch_c[4] = {4, 8, 4, 4};
         float best_ms = 1e30f;
         best.n_trials = 0;
         for (int f = 0; f < 2; ++f)
-            for (int b = 0; b < 2; ++b) {
-                for (int s = 0; s < n; ++s)
-                    trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * factors[f] : descs[s].cell_size;
+            for (int b = 0; b < 4; ++b) {
+                if (fixed_lanes && lanes_c[b] != fixed_lanes) continue;
+                if (lanes_c[b] == 4 && lane_cap(max_cap, 4) > 255) continue;
+                set_trial(factors[f], lanes_c[b]);
                 float ms = 0.0f;
-                sph_status st = time_config(trial, alloc, stream, batches[b], 5, &ms);
+                sph_status st = time_config(trial, alloc, stream, batch_c[b], 5, &ms);
                 if (st != SPH_OK) return st;
                 const int k = best.n_trials++;
                 best.trial_cell_factor[k] = factors[f];
-                best.trial_batch[k] = batches[b];
+                best.trial_batch[k] = batch_c[b];
+                best.trial_lanes[k] = lanes_c[b];
                 best.trial_ms[k] = ms;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best.cell_factor = factors[f];
-                    best.gather_batch = batches[b];
+                    best.gather_batch = batch_c[b];
+                    best.lanes = lanes_c[b];
                 }
             }
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -900,8 +967,7 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
     }
     best.tuned = 1;
     best.from_cache = cached ? 1 : 0;
-    for (int s = 0; s < n; ++s)
-        trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * best.cell_factor : descs[s].cell_size;
+    set_trial(best.cell_factor, best.lanes);
     sph_status st = create_impl(trial.data(), n, alloc, stream, out, best.gather_batch);
     if (st == SPH_OK) (*out)->tuning = best;
     return st;
@@ -959,6 +1025,7 @@ sph_status sph_get_tuning(sph_ctx *c, sph_tuning *out)
     *out = c->tuning;
     if (!c->tuning.tuned) {
         out->gather_batch = c->batch;
+        out->lanes = c->P.lanes;
         out->cell_factor = c->scenes[0].cell / (4.0f * (float)(c->scenes[0].two_r * 0.5f));
     }
     return SPH_OK;

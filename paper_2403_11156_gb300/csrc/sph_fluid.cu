@@ -1,36 +1,21 @@
 // sph_fluid.cu -- per-particle sweeps of the DFSPH step.
 //
-// One thread owns one fluid particle in grid order.  The density sweep walks the 27-cell
-// neighbourhood (9 contiguous index ranges) once per step, applies the float neighbour
-// predicate and records each neighbour's index in a k-major list; every later sweep of
-// the step (divergence and density Jacobi passes, non-pressure forces, warm starts)
-// gathers through that list.  The solvers' error sums are accumulated per block in FP64
-// and reduced in a fixed order by the last block of each scene, which also decides the
-// loop condition on the device (CUDA graph conditional node).
-#include "sph_internal.cuh"
+// T threads (lanes, T = 1, 2 or 4) own one fluid particle in grid order.  The density
+// sweep walks the (2R+1)^3-cell neighbourhood ((2R+1)^2 contiguous index ranges) once
+// per step, lane s testing every T-th candidate of each range, and records each
+// neighbour's index in the lane's sub-list; every later sweep of the step (divergence
+// and density Jacobi passes, non-pressure forces, warm starts) gathers through those
+// sub-lists and combines the T partial sums with warp shuffles.  The solvers' error sums
+// are accumulated per block in FP64 and reduced in a fixed order by the last block of
+// each scene, which also decides the loop condition on the device (CUDA graph
+// conditional node).
+#include "sph_sweep.cuh"
 
 #include <math_constants.h>
 
 namespace sph {
 
 namespace {
-
-// Cubic spline (Sec. 3.2 with h = 4r, Sec. 5): W = sigma w(q), grad W = kgrad g(q) x/|x|.
-__device__ __forceinline__ float spline_w(float q)
-{
-    if (q <= 0.5f) return fmaf(6.0f * q, q * q, fmaf(-6.0f * q, q, 1.0f));
-    float t = fmaxf(1.0f - q, 0.0f);
-    return 2.0f * t * t * t;
-}
-// grad W_ij = factor * x_ij; zero for coincident particles.
-__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
-{
-    if (!(r2 > 0.0f)) return 0.0f;
-    float rinv = rsqrtf(r2);
-    float q = r2 * rinv * sc.inv_h;
-    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
-    return sc.kgrad * g * rinv;
-}
 
 __device__ __forceinline__ void set_w(float4 *p, int64_t i, float w)
 {
@@ -119,56 +104,24 @@ __global__ void k_step_begin(Ptrs P)
     st.maxv2 = 0.0f;
 }
 
-// Visit the entries [0, n) of particle i's k-major list in batches of U: the U index loads
-// of a batch are issued together, then the U visits, whose gathers the compiler can then
-// keep in flight together (the visits only accumulate in registers).  The visiting order,
-// and so the floating-point summation order, is the list order.
-template <int U, bool NC = true, typename F>
-__device__ __forceinline__ void for_list(const int32_t *__restrict__ list, int64_t NF, int64_t i, int n,
-                                         F &&visit)
-{
-    // NC: the list is read-only for the whole kernel (read-only data path); otherwise
-    // plain loads, for a list this thread has just written
-    auto ld = [&](int k) { return NC ? __ldg(list + (int64_t)k * NF + i) : list[(int64_t)k * NF + i]; };
-    int k = 0;
-    for (; k + U <= n; k += U) {
-        int32_t j[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) j[u] = ld(k + u);
-#pragma unroll
-        for (int u = 0; u < U; ++u) visit(j[u]);
-    }
-    for (; k < n; ++k) visit(ld(k));
-}
-
-// Visit the contiguous candidate range [jb, je) of a grid row in batches of U: the U
-// position loads of a batch are issued before any visit, in index order.
-template <int U, typename F>
-__device__ __forceinline__ void for_range(const float4 *__restrict__ pos, uint32_t jb, uint32_t je, F &&visit)
-{
-    uint32_t j = jb;
-    for (; j + U <= je; j += U) {
-        float4 p[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) p[u] = __ldg(pos + j + u);
-#pragma unroll
-        for (int u = 0; u < U; ++u) visit(j + u, p[u]);
-    }
-    for (; j < je; ++j) visit(j, __ldg(pos + j));
-}
-
 // ------------------------------------------------------------------------------------
 // Density (Eq. density + Sec. 3.5 boundary term), DFSPH alpha, neighbour lists, and the
 // gate of the divergence warm start (D rho/Dt with the velocities at step start).
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
 {
     kernel_enter(P.ctl, KID_DENSITY);
-    BlockCtx c = fluid_ctx(P);
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
-    int nn_f = 0, nn_b = 0;
+    const int64_t i = c.i, NF = P.NF;
+    const int s = c.s;
+    const bool gate = sc.warm != 0 && sc.div_on;
+    int nn_f = 0, nn_b = 0;  // this lane's neighbours (may exceed its capacity)
+    // this lane's shares of rho - m W(0), sum grad W, sum |grad W|^2 and D rho/Dt
+    float rho_l = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, s2 = 0.0f, div_l = 0.0f;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c.valid) {
-        const int64_t i = c.i, NF = P.NF;
-        const float4 pi = P.pos_s[i];
+        pi = P.pos_s[i];
         const float4 vi = P.vel_s[i];
         const int32_t cx = cell_coord(pi.x, sc.origin[0], sc.cell, sc.dims[0]);
         const int32_t cy = cell_coord(pi.y, sc.origin[1], sc.cell, sc.dims[1]);
@@ -176,12 +129,12 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         const int32_t R = sc.R;
         const int32_t x0 = max(cx - R, 0), x1 = min(cx + R, sc.dims[0] - 1);
         const float h2 = sc.h2;
-        const int cap_f = sc.cap_f, cap_b = sc.cap_b;
+        const int lcap_f = sc.lcap_f, lcap_b = sc.lcap_b;
         int32_t *__restrict__ nbr = P.nbr;
         int32_t *__restrict__ bnbr = P.bnbr;
-        // phase 1: the float predicate over the (2R+1)^3-cell stencil ((2R+1)^2
-        // contiguous index ranges) only records neighbours; keeping the expensive per-pair work out of this
-        // loop keeps the warp converged while most candidates are rejected
+        // phase 1: the float predicate over the stencil's index ranges only records
+        // neighbours; keeping the per-pair work out of this loop keeps the warp converged
+        // while most candidates are rejected
         for (int32_t dz = -R; dz <= R; ++dz) {
             const int32_t z = cz + dz;
             if (z < 0 || z >= sc.dims[2]) continue;
@@ -190,54 +143,52 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
                 if (y < 0 || y >= sc.dims[1]) continue;
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
                 const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
-                for_range<2>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
+                for_range<4, T>(P.pos_s, jb + (uint32_t)s, je, [&](uint32_t j, float4 pj) {
                     float dx, dy2, dz2;
                     const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
                     if (d2 < h2 && (int64_t)j != i) {
-                        if (nn_f < cap_f) nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
+                        if (nn_f < lcap_f) nbr[list_at<T>(NF, i, nn_f, s)] = (int32_t)j;
                         ++nn_f;
                     }
                 });
                 if (sc.nb > 0) {
                     const uint32_t bb = P.bcell_start[row + x0], be = P.bcell_start[row + x1 + 1];
-                    for_range<1>(P.bpos_s, bb, be, [&](uint32_t b, float4 pb) {
+                    for_range<1, T>(P.bpos_s, bb + (uint32_t)s, be, [&](uint32_t b, float4 pb) {
                         float dx, dy2, dz2;
                         const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
                         if (d2 < h2) {
-                            if (nn_b < cap_b) bnbr[(int64_t)nn_b * NF + i] = (int32_t)b;
+                            if (nn_b < lcap_b) bnbr[list_at<T>(NF, i, nn_b, s)] = (int32_t)b;
                             ++nn_b;
                         }
                     });
                 }
             }
         }
-        const int nf = min(nn_f, cap_f), nb = min(nn_b, cap_b);
-        // phase 2: density, alpha and the warm-start gate over the recorded lists (the
-        // same pairs in the same order as the stencil walk)
-        const bool gate = sc.warm != 0 && sc.div_on;
-        float w_sum = 0.0f, s1x = 0.0f, s1y = 0.0f, s1z = 0.0f, s2 = 0.0f, div_f = 0.0f;
-        for_list<2, false>(nbr, NF, i, nf, [&](int32_t j) {
+        // phase 2: density, alpha and the warm-start gate over the recorded sub-list
+        float w_sum = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f, div_f = 0.0f;
+        for_list<2, T, false>(nbr, NF, i, s, min(nn_f, lcap_f), [&](int32_t j) {
             const float4 pj = __ldg(P.pos_s + j);
             float dx, dy2, dz2;
             const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
             w_sum += spline_w(sqrtf(d2) * sc.inv_h);
             const float f = grad_factor(sc, d2);
             const float gx = f * dx, gy = f * dy2, gz = f * dz2;
-            s1x += gx; s1y += gy; s1z += gz;
+            fx += gx; fy += gy; fz += gz;
             s2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, s2)));
             if (gate) {
                 const float4 vj = __ldg(P.vel_s + j);
                 div_f += (vi.x - vj.x) * gx + (vi.y - vj.y) * gy + (vi.z - vj.z) * gz;
             }
         });
-        float rho = sc.m * sc.sigma * (1.0f + w_sum);
-        s1x *= sc.m; s1y *= sc.m; s1z *= sc.m;
+        rho_l = sc.m * sc.sigma * w_sum;
+        s1x = sc.m * fx; s1y = sc.m * fy; s1z = sc.m * fz;
         s2 *= sc.m * sc.m;
-        float div = sc.m * div_f;
+        div_l = sc.m * div_f;
+        const int nb = min(nn_b, lcap_b);
         if (nb > 0) {
             float wb = 0.0f, divb = 0.0f;
             const bool moving = sc.has_moving != 0;
-            for_list<1, false>(bnbr, NF, i, nb, [&](int32_t b) {
+            for_list<1, T, false>(bnbr, NF, i, s, nb, [&](int32_t b) {
                 const float4 pb = __ldg(P.bpos_s + b);
                 float dx, dy2, dz2;
                 const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
@@ -251,50 +202,63 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
                     divb += (vi.x - vb.x) * gx + (vi.y - vb.y) * gy + (vi.z - vb.z) * gz;
                 }
             });
-            rho += sc.sigma * wb;
-            div += divb;
+            rho_l += sc.sigma * wb;
+            div_l += divb;
         }
+    }
+    // combine the lanes (all threads of the warp take part)
+    rho_l = group_sum<T>(rho_l);
+    s1x = group_sum<T>(s1x); s1y = group_sum<T>(s1y); s1z = group_sum<T>(s1z);
+    s2 = group_sum<T>(s2);
+    div_l = group_sum<T>(div_l);
+    const uint32_t pk_f = group_sum<T>(lane_pack<T>(min(nn_f, sc.lcap_f), s));
+    const uint32_t pk_b = group_sum<T>(lane_pack<T>(min(nn_b, sc.lcap_b), s));
+    const int tot_f = group_sum<T>(nn_f), tot_b = group_sum<T>(nn_b);
+    const bool lane_over = nn_f > sc.lcap_f || nn_b > sc.lcap_b;
+    if (c.valid && s == 0) {
+        const float rho = fmaf(sc.m, sc.sigma, rho_l);
         const float den = fmaf(s1x, s1x, fmaf(s1y, s1y, fmaf(s1z, s1z, s2)));
         const float alpha = den > sc.eps_alpha ? rho / den : 0.0f;
         P.alpha[i] = alpha;
         set_w(P.vel_s, i, rho);
-        P.nnf[i] = nf;
-        P.nnb[i] = nb;
+        P.nnf[i] = (int32_t)pk_f;
+        P.nnb[i] = (int32_t)pk_b;
         float kv0 = 0.0f;
-        if (gate && div > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
+        if (gate && div_l > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
         P.kvsum[i] = kv0;
         set_w(P.pos_s, i, kv0 / rho);
     }
-    int mf = warp_max(nn_f), mb = warp_max(nn_b);
+    const int mf = warp_max(tot_f), mb = warp_max(tot_b);
+    const unsigned over = __ballot_sync(0xffffffffu, lane_over);
     if ((threadIdx.x & 31) == 0) {
         if (mf > 0) atomicMax(&c.st->max_nn_f, mf);
         if (mb > 0) atomicMax(&c.st->max_nn_b, mb);
-        if (mf > sc.cap_f || mb > sc.cap_b) atomicOr(&c.st->flags, 1);
+        if (mf > sc.cap_f || mb > sc.cap_b || over) atomicOr(&c.st->flags, 1);
     }
 }
 
 // ------------------------------------------------------------------------------------
-// D rho_i/Dt = sum_j m (v_i - v_j).grad W_ij + sum_b Psi_b (v_i - v_b).grad W_ib
-// (SPH divergence of Sec. 3.2 in the continuity equation, boundary per Sec. 3.5).
+// This lane's share of D rho_i/Dt = sum_j m (v_i - v_j).grad W_ij + sum_b Psi_b (v_i -
+// v_b).grad W_ib (SPH divergence of Sec. 3.2 in the continuity equation, boundary per
+// Sec. 3.5); group_sum of the shares is the full sum.
 constexpr int kBatch = 4;
 
-template <int B = kBatch>
-__device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi,
-                                         float4 vi, const float4 *__restrict__ V)
+template <int B, int T>
+__device__ __forceinline__ float drho_dt_lane(const Ptrs &P, const SceneDev &sc, int64_t i, int s, float4 pi,
+                                              float4 vi, const float4 *__restrict__ V)
 {
     const int64_t NF = P.NF;
     float acc = 0.0f;
-    for_list<B>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
+    for_list<B, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
         const float4 pj = __ldg(P.pos_s + j);
         const float4 vj = __ldg(V + j);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         acc = fmaf(f, (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz, acc);
     });
-    acc *= sc.m;
     float accb = 0.0f;
     const bool moving = sc.has_moving != 0;
-    for_list<4>(P.bnbr, NF, i, P.nnb[i], [&](int32_t b) {
+    for_list<4, T>(P.bnbr, NF, i, s, lane_count<T>(P.nnb[i], s), [&](int32_t b) {
         const float4 pb = __ldg(P.bpos_s + b);
         const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
         const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -305,31 +269,36 @@ __device__ __forceinline__ float drho_dt(const Ptrs &P, const SceneDev &sc, int6
         }
         accb = fmaf(f, ux * dx + uy * dy + uz * dz, accb);
     });
-    return acc + accb;
+    return fmaf(sc.m, acc, accb);
 }
 
 // Pass A of a Jacobi iteration (Alg. ppe_solver "refine p"): the source term of
 // Eq. velocity_source (solver 0) or Eq. density_source with rho* (solver 1), the
 // stiffness kappa_i = alpha_i e_i / dt^(1 or 2), and the block's FP64 error partial.
-template <int S, int B>
+template <int S, int B, int T>
 __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
     __shared__ int s_last;
     kernel_enter(P.ctl, (KID_PASS_A0 + S));
-    BlockCtx c = fluid_ctx(P);
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
     if (!solver_active(sc, st, S)) return;  // uniform per block
     const float dt = st.dt;
-    double e = 0.0;
+    const float4 *V = S == 0 ? P.vel_s : P.vel_c;
+    const int64_t i = c.i;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+    float D = 0.0f;
     if (c.valid) {
-        const int64_t i = c.i;
-        const float4 *V = S == 0 ? P.vel_s : P.vel_c;
-        const float4 pi = P.pos_s[i];
-        const float4 vi = V[i];
+        pi = P.pos_s[i];
+        vi = V[i];
+        D = drho_dt_lane<B, T>(P, sc, i, c.s, pi, vi, V);
+    }
+    D = group_sum<T>(D);
+    double e = 0.0;
+    if (c.valid && c.s == 0) {
         const float rho = vi.w;
-        const float D = drho_dt<B>(P, sc, i, pi, vi, V);
         float ei, kappa;
         if (S == 0) {
             ei = fmaxf(D, 0.0f);
@@ -348,15 +317,18 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
         P.partial[blockIdx.x] = bsum;
         __threadfence();
         uint32_t prev = atomicAdd(&st.counter, 1u);
-        s_last = (prev == (uint32_t)sc.fblk_count - 1u);
+        s_last = (prev == (uint32_t)sc.tblk_count - 1u);
     }
     __syncthreads();
     if (!s_last) return;
-    // last block of this scene: fixed-order sum of the scene's partials
+    // last block of this scene: fixed-order sum of the scene's partials (L2 loads, several
+    // in flight per thread)
     __threadfence();
     double t = 0.0;
-    const volatile double *part = P.partial;
-    for (int k = threadIdx.x; k < sc.fblk_count; k += kBlock) t += part[sc.fblk_first + k];
+    const double *part = P.partial + sc.tblk_first;
+    const int cnt = sc.tblk_count;
+#pragma unroll 8
+    for (int k = threadIdx.x; k < cnt; k += kBlock) t += __ldcg(part + k);
     double total = block_sum(t, sh);
     if (threadIdx.x == 0) {
         double err = sc.nf > 0 ? total / (double)sc.nf / (double)sc.rho0 : 0.0;
@@ -373,42 +345,48 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 // Eq. rigid_pressure per unit fluid mass:
 //   v_i -= dt [ sum_j m (k_i/rho_i + k_j/rho_j) grad W_ij + sum_b Psi_b (k_i/rho_i) grad W_ib ]
 // WARM = 1 applies the warm-start kappas (no loop bookkeeping).
-template <int S, int WARM, int B>
+template <int S, int WARM, int B, int T>
 __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
 {
     __shared__ int s_last;
     kernel_enter(P.ctl, (WARM ? KID_PASS_B0W + S : KID_PASS_B0 + S));
-    BlockCtx c = fluid_ctx(P);
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
-    bool run = WARM ? (sc.warm != 0 && (S == 1 || sc.div_on)) : (st.pending[S] != 0);
-    if (run && c.valid) {
+    const bool run = WARM ? (sc.warm != 0 && (S == 1 || sc.div_on)) : (st.pending[S] != 0);  // uniform per block
+    if (run) {
         const int64_t i = c.i, NF = P.NF;
-        float4 *V = S == 0 ? P.vel_s : P.vel_c;
-        const float4 pi = P.pos_s[i];
-        const float ki = pi.w;
+        const int s = c.s;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        for_list<B>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
-            const float4 pj = __ldg(P.pos_s + j);
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
-            ax = fmaf(f, dx, ax); ay = fmaf(f, dy, ay); az = fmaf(f, dz, az);
-        });
-        ax *= sc.m; ay *= sc.m; az *= sc.m;
-        if (ki != 0.0f) {
-            float bx = 0.0f, by = 0.0f, bz = 0.0f;
-            for_list<4>(P.bnbr, NF, i, P.nnb[i], [&](int32_t b) {
-                const float4 pb = __ldg(P.bpos_s + b);
-                const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
-                const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                bx = fmaf(f, dx, bx); by = fmaf(f, dy, by); bz = fmaf(f, dz, bz);
+        if (c.valid) {
+            const float4 pi = P.pos_s[i];
+            const float ki = pi.w;
+            for_list<B, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
+                const float4 pj = __ldg(P.pos_s + j);
+                const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
+                ax = fmaf(f, dx, ax); ay = fmaf(f, dy, ay); az = fmaf(f, dz, az);
             });
-            ax = fmaf(ki, bx, ax); ay = fmaf(ki, by, ay); az = fmaf(ki, bz, az);
+            ax *= sc.m; ay *= sc.m; az *= sc.m;
+            if (ki != 0.0f) {
+                float bx = 0.0f, by = 0.0f, bz = 0.0f;
+                for_list<4, T>(P.bnbr, NF, i, s, lane_count<T>(P.nnb[i], s), [&](int32_t b) {
+                    const float4 pb = __ldg(P.bpos_s + b);
+                    const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
+                    const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    bx = fmaf(f, dx, bx); by = fmaf(f, dy, by); bz = fmaf(f, dz, bz);
+                });
+                ax = fmaf(ki, bx, ax); ay = fmaf(ki, by, ay); az = fmaf(ki, bz, az);
+            }
         }
-        const float dt = st.dt;
-        float4 v = V[i];
-        v.x -= dt * ax; v.y -= dt * ay; v.z -= dt * az;
-        V[i] = v;
+        ax = group_sum<T>(ax); ay = group_sum<T>(ay); az = group_sum<T>(az);
+        if (c.valid && s == 0) {
+            float4 *V = S == 0 ? P.vel_s : P.vel_c;
+            const float dt = st.dt;
+            float4 v = V[i];
+            v.x -= dt * ax; v.y -= dt * ay; v.z -= dt * az;
+            V[i] = v;
+        }
     }
     if (WARM) return;
     __syncthreads();
@@ -422,16 +400,16 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
     // last block of the whole launch: advance the iteration counters, decide the loop
     __threadfence();
     uint32_t any = 0;
-    for (int s = 0; s < P.nscenes; ++s) {
-        const SceneDev &q = P.scenes[s];
-        SceneState &qs = P.st[s];
+    for (int q = 0; q < P.nscenes; ++q) {
+        const SceneDev &qd = P.scenes[q];
+        SceneState &qs = P.st[q];
         if (qs.pending[S]) {
             qs.it[S] += 1;
             qs.total_it[S] += 1;
             qs.pending[S] = 0;
-            if (!solver_active(q, qs, S) && qs.err[S] > (double)q.eta[S]) qs.flags |= 2;
+            if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
         }
-        if (solver_active(q, qs, S)) any = 1;
+        if (solver_active(qd, qs, S)) any = 1;
     }
     uint32_t guard = ++P.ctl->loop_guard;
     if (guard > 100000u) {
@@ -451,38 +429,47 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
 //   lap v_i = 2(d+2) sum_j (m/rho_j) (v_ij . x_ij)/(|x_ij|^2 + 0.01 h^2) grad W_ij,
 // or XSPH smoothing c sum_j (m/rho_j)(v_j - v_i) W_ij.  Writes v* to the canonical
 // velocity array and clears the density-solve stiffness sum.
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 {
     kernel_enter(P.ctl, KID_NONP);
-    BlockCtx c = fluid_ctx(P);
-    if (!c.valid) return;
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     const int64_t i = c.i, NF = P.NF;
-    const float dt = c.st->dt;
-    const float4 pi = P.pos_s[i];
-    const float4 vi = P.vel_s[i];
-    const float rho_i = vi.w;
-    float ax = sc.g[0], ay = sc.g[1], az = sc.g[2];
+    const int s = c.s;
+    float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-    if (sc.visc_mode == 1 || sc.visc_mode == 2) {
-        const float reg = 0.01f * sc.h2;
-        const bool lap = sc.visc_mode == 1;
-        for_list<kBatch>(P.nbr, NF, i, P.nnf[i], [&](int32_t j) {
-            const float4 pj = __ldg(P.pos_s + j);
-            const float4 vj = __ldg(P.vel_s + j);
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (lap) {
-                const float f = grad_factor(sc, r2);
-                const float s = f * (ux * dx + uy * dy + uz * dz) / ((r2 + reg) * vj.w);
-                sx = fmaf(s, dx, sx); sy = fmaf(s, dy, sy); sz = fmaf(s, dz, sz);
-            } else {
-                const float w = spline_w(sqrtf(r2) * sc.inv_h) / vj.w;
-                sx = fmaf(-w, ux, sx); sy = fmaf(-w, uy, sy); sz = fmaf(-w, uz, sz);
-            }
-        });
+    const bool visc = sc.visc_mode == 1 || sc.visc_mode == 2;  // uniform per block
+    if (c.valid) {
+        vi = P.vel_s[i];
+        if (visc) {
+            const float4 pi = P.pos_s[i];
+            const float reg = 0.01f * sc.h2;
+            const bool lap = sc.visc_mode == 1;
+            for_list<kBatch, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
+                const float4 pj = __ldg(P.pos_s + j);
+                const float4 vj = __ldg(P.vel_s + j);
+                const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (lap) {
+                    const float f = grad_factor(sc, r2);
+                    const float q = f * (ux * dx + uy * dy + uz * dz) / ((r2 + reg) * vj.w);
+                    sx = fmaf(q, dx, sx); sy = fmaf(q, dy, sy); sz = fmaf(q, dz, sz);
+                } else {
+                    const float w = spline_w(sqrtf(r2) * sc.inv_h) / vj.w;
+                    sx = fmaf(-w, ux, sx); sy = fmaf(-w, uy, sy); sz = fmaf(-w, uz, sz);
+                }
+            });
+        }
     }
+    if (visc) {
+        sx = group_sum<T>(sx); sy = group_sum<T>(sy); sz = group_sum<T>(sz);
+    }
+    if (!c.valid || s != 0) return;
+    const float dt = c.st->dt;
+    const float rho_i = vi.w;
+    const float ax = sc.g[0], ay = sc.g[1], az = sc.g[2];
     float4 v = vi;
     if (sc.visc_mode == 1) {
         const float k = 10.0f * sc.mu * sc.m / rho_i;
@@ -504,19 +491,25 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 // v* gates half the previous step's stiffness (kept as kappa dt^2); the learned mode
 // stores the network's input features instead (rho/rho0 - 1, dt Drho/Dt/rho0,
 // (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
 {
     kernel_enter(P.ctl, KID_WARM);
-    BlockCtx c = fluid_ctx(P);
-    if (!c.valid) return;
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
-    if (sc.warm == 0) return;
+    if (sc.warm == 0) return;  // uniform per block
     const int64_t i = c.i;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+    float D = 0.0f;
+    if (c.valid) {
+        pi = P.pos_s[i];
+        vi = P.vel_c[i];
+        D = drho_dt_lane<kBatch, T>(P, sc, i, c.s, pi, vi, P.vel_c);
+    }
+    D = group_sum<T>(D);
+    if (!c.valid || c.s != 0) return;
     const float dt = c.st->dt;
-    const float4 pi = P.pos_s[i];
-    const float4 vi = P.vel_c[i];
     const float rho = vi.w;
-    const float D = drho_dt(P, sc, i, pi, vi, P.vel_c);
     const float dev = fmaf(dt, D, rho - sc.rho0);
     // the network's inputs are recorded in both warm-start modes (the previous-step mode
     // produces the training data)
@@ -524,7 +517,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     float4 f;
     f.x = rho / sc.rho0 - 1.0f;
     f.y = dt * D / sc.rho0;
-    f.z = (float)(P.nnf[i] + P.nnb[i]) / 33.0f;
+    f.z = (float)(nn_total(P.nnf[i], T) + nn_total(P.nnb[i], T)) / 33.0f;
     f.w = P.kprev_s[i] / (dt * dt) / kref;
     reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;
@@ -654,32 +647,51 @@ void launch_step_begin(const Ptrs &P, cudaStream_t s)
     int b = (P.nscenes + t - 1) / t;
     k_step_begin<<<b, t, 0, s>>>(P);
 }
-void launch_density_alpha(const Ptrs &P, cudaStream_t s) { k_density_alpha<<<P.nfblk, kBlock, 0, s>>>(P); }
+// Sweep kernels take T from the context (threads per particle) and the gather batch B
+// of the Jacobi passes from its tuning: (T, B) in {(1, 4), (1, 8), (2, 4), (4, 4)}.
+void launch_density_alpha(const Ptrs &P, cudaStream_t s)
+{
+#define SPH_L(T) k_density_alpha<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
 void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s)
 {
-    if (batch == 8) {
-        if (solver == 0) k_pass_a<0, 8><<<P.nfblk, kBlock, 0, s>>>(P);
-        else k_pass_a<1, 8><<<P.nfblk, kBlock, 0, s>>>(P);
-    } else {
-        if (solver == 0) k_pass_a<0, 4><<<P.nfblk, kBlock, 0, s>>>(P);
-        else k_pass_a<1, 4><<<P.nfblk, kBlock, 0, s>>>(P);
-    }
+#define SPH_A(S, B, T) k_pass_a<S, B, T><<<P.ntblk, kBlock, 0, s>>>(P)
+    if (P.lanes == 4) { if (solver == 0) SPH_A(0, 4, 4); else SPH_A(1, 4, 4); }
+    else if (P.lanes == 2) { if (solver == 0) SPH_A(0, 4, 2); else SPH_A(1, 4, 2); }
+    else if (batch == 8) { if (solver == 0) SPH_A(0, 8, 1); else SPH_A(1, 8, 1); }
+    else { if (solver == 0) SPH_A(0, 4, 1); else SPH_A(1, 4, 1); }
+#undef SPH_A
 }
 void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphConditionalHandle h, int use_handle,
                    cudaStream_t s)
 {
-#define SPH_PASS_B(S, W, B) k_pass_b<S, W, B><<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle)
-    if (batch == 8) {
-        if (solver == 0) { if (warm) SPH_PASS_B(0, 1, 8); else SPH_PASS_B(0, 0, 8); }
-        else { if (warm) SPH_PASS_B(1, 1, 8); else SPH_PASS_B(1, 0, 8); }
-    } else {
-        if (solver == 0) { if (warm) SPH_PASS_B(0, 1, 4); else SPH_PASS_B(0, 0, 4); }
-        else { if (warm) SPH_PASS_B(1, 1, 4); else SPH_PASS_B(1, 0, 4); }
-    }
-#undef SPH_PASS_B
+#define SPH_B(S, W, B, T) k_pass_b<S, W, B, T><<<P.ntblk, kBlock, 0, s>>>(P, h, use_handle)
+#define SPH_BW(B, T)                                                 \
+    do {                                                             \
+        if (solver == 0) { if (warm) SPH_B(0, 1, B, T); else SPH_B(0, 0, B, T); } \
+        else { if (warm) SPH_B(1, 1, B, T); else SPH_B(1, 0, B, T); }             \
+    } while (0)
+    if (P.lanes == 4) SPH_BW(4, 4);
+    else if (P.lanes == 2) SPH_BW(4, 2);
+    else if (batch == 8) SPH_BW(8, 1);
+    else SPH_BW(4, 1);
+#undef SPH_BW
+#undef SPH_B
 }
-void launch_nonpressure(const Ptrs &P, cudaStream_t s) { k_nonpressure<<<P.nfblk, kBlock, 0, s>>>(P); }
-void launch_warm_density(const Ptrs &P, cudaStream_t s) { k_warm_density<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_nonpressure(const Ptrs &P, cudaStream_t s)
+{
+#define SPH_L(T) k_nonpressure<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
+void launch_warm_density(const Ptrs &P, cudaStream_t s)
+{
+#define SPH_L(T) k_warm_density<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
 void launch_advect(const Ptrs &P, cudaStream_t s) { k_advect<<<P.nfblk, kBlock, 0, s>>>(P); }
 void launch_step_end(const Ptrs &P, cudaStream_t s) { k_step_end<<<1, 128, 0, s>>>(P); }
 void launch_set_dt(const Ptrs &P, float dt, cudaStream_t s) { k_set_dt<<<1, 1, 0, s>>>(P.ctl, dt); }

@@ -4,7 +4,8 @@
 //   fluid, current sorted order  pos_s  float4 (x, y, z, kappa/rho of the current sweep)
 //                                vel_s  float4 (v, rho)
 //   fluid, canonical order       pos_c, vel_c (same packing), kprev_c, kvprev_c, id_c
-//   neighbour lists              nbr[k * NF + i], bnbr[k * NF + i]  (k-major: coalesced)
+//   neighbour lists              nbr, bnbr: T interleaved sub-lists per particle, entry k
+//                                of sub-list s at ((k NF) + i) T + s (k-major: coalesced)
 //   boundary, original order     bx_o float4 (x, 0), bv_o float4, br0 float4, bbody int32
 //   boundary, sorted order       bpos_s float4 (x, Psi), bvel_s float4 (v_b, 0)
 // "Canonical" is the sorted order of the previous step: the reorder gathers canonical ->
@@ -44,7 +45,9 @@ struct SceneDev {
     int32_t body_off, nbody;
     int32_t fblk_first, fblk_count;   // fluid particle blocks of this scene
     int32_t bblk_first, bblk_count;   // boundary particle blocks
-    int32_t cap_f, cap_b;             // neighbour list capacities
+    int32_t tblk_first, tblk_count;   // sweep blocks (kBlock / lanes particles each)
+    int32_t cap_f, cap_b;             // neighbour list capacities (per particle)
+    int32_t lcap_f, lcap_b;           // capacities of one lane's sub-list
     int32_t R;                        // stencil radius in cells: 1 (cell >= h), 2 (cell >= h/2)
     float cg_tol;
     int32_t cg_max;
@@ -155,14 +158,17 @@ struct Ptrs {
     BodyDev *bodies;
     const int32_t *fblk_scene;        // scene of each fluid block
     const int32_t *bblk_scene;        // scene of each boundary block
+    const int32_t *tblk_scene;        // scene of each sweep block
     int32_t nfblk, nbblk, nscenes, nbodies_total;
+    int32_t ntblk;                    // sweep blocks
+    int32_t lanes;                    // threads per fluid particle in the sweeps: 1, 2, 4
     int64_t NF, NB, NC;               // totals: fluid, boundary, cells
     // fluid
     float4 *pos_s, *vel_s, *pos_c, *vel_c;
     float *kprev_c, *kvprev_c, *kprev_s, *kvprev_s;
     float *ksum, *kvsum, *alpha, *k0;
     int32_t *id_c, *id_s;
-    int32_t *nnf, *nnb;
+    int32_t *nnf, *nnb;               // sub-list lengths, packed (32 / lanes bits each)
     int32_t *nbr, *bnbr;
     float *feat;                      // [NF][4]
     // grid scratch (fluid)
@@ -178,13 +184,13 @@ struct Ptrs {
     uint32_t *bcell_count, *bcell_start;
     uint32_t *bkey_tmp, *bslot_tmp, *bsid_tmp, *bsrc_tmp, *bcell_tmp;
     // reductions
-    double *partial;                  // [nfblk]
-    double *body_partial;             // [body][6][nfblk] per-block force/torque partials
+    double *partial;                  // [ntblk]
+    double *body_partial;             // [body][6][ntblk] per-block force/torque partials
     uint64_t *scan_status;            // [tiles]
     int32_t scan_tiles;
     // implicit viscosity CG
     float4 *cg_r, *cg_p, *cg_ap;
-    double *cg_dots;                  // per-block partials [nfblk][2]
+    double *cg_dots;                  // per-block partials [max(nfblk, ntblk)][2]
     // network
     float *mlp_w;                     // device parameter block (float)
 };
@@ -206,6 +212,15 @@ __device__ __forceinline__ float pred_d2(float4 a, float4 b, float &dx, float &d
     dy = __fsub_rn(a.y, b.y);
     dz = __fsub_rn(a.z, b.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Neighbour count of a particle from its packed sub-list lengths.
+__device__ __forceinline__ int32_t nn_total(int32_t packed, int32_t lanes)
+{
+    const uint32_t p = (uint32_t)packed;
+    if (lanes == 1) return (int32_t)p;
+    if (lanes == 2) return (int32_t)((p & 0xFFFFu) + (p >> 16));
+    return (int32_t)((p & 0xFFu) + ((p >> 8) & 0xFFu) + ((p >> 16) & 0xFFu) + (p >> 24));
 }
 
 enum SortWhat { SORT_FLUID = 0, SORT_BOUNDARY = 1 };

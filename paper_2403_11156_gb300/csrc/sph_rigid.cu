@@ -7,27 +7,11 @@
 //  * the reaction of Eq. rigid_pressure_symmetric: F_{b<-i} = m Psi_b (kappa_i/rho_i)
 //    grad W_ib with the step's total applied kappa (divergence + density solves), summed
 //    per body with its torque in FP64 and reduced in a fixed order.
-#include "sph_internal.cuh"
+#include "sph_sweep.cuh"
 
 namespace sph {
 
 namespace {
-
-__device__ __forceinline__ float spline_w(float q)
-{
-    if (q <= 0.5f) return fmaf(6.0f * q, q * q, fmaf(-6.0f * q, q, 1.0f));
-    float t = fmaxf(1.0f - q, 0.0f);
-    return 2.0f * t * t * t;
-}
-
-__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
-{
-    if (!(r2 > 0.0f)) return 0.0f;
-    float rinv = rsqrtf(r2);
-    float q = r2 * rinv * sc.inv_h;
-    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
-    return sc.kgrad * g * rinv;
-}
 
 // Boundary particles of moving bodies follow their body (original order).
 __global__ void __launch_bounds__(kBlock) k_boundary_update(Ptrs P)
@@ -103,21 +87,22 @@ __device__ double block_sum_d(double v, double *sh)
     return t;
 }
 
-// Force and torque of the fluid on each body of the scene for the step just solved.
+// Force and torque of the fluid on each body of the scene for the step just solved (the
+// T lanes of a particle walk its T boundary sub-lists; the block sums add all lanes).
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
     kernel_enter(P.ctl, KID_BFORCE);
-    const SceneDev &sc = P.scenes[P.fblk_scene[blockIdx.x]];
-    if (sc.nbody == 0) return;
-    int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
-    const bool valid = local < sc.nf;
-    const int64_t i = sc.f_off + local;
+    const Lane<T> c = lane_ctx<T>(P);
+    const SceneDev &sc = *c.sc;
+    if (sc.nbody == 0) return;  // uniform per block
+    const int64_t i = c.i, NF = P.NF;
     int nb = 0;
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     float kt = 0.0f;
-    if (valid) {
-        nb = P.nnb[i];
+    if (c.valid) {
+        nb = lane_count<T>(P.nnb[i], c.s);
         pi = P.pos_s[i];
         kt = (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
     }
@@ -128,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     __syncthreads();
     unsigned long long mine = 0ull;
     for (int t = 0; t < nb; ++t) {
-        const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * P.NF + i]];
+        const int32_t k = P.bbody_s[P.bnbr[list_at<T>(NF, i, t, c.s)]];
         if (k >= 0) mine |= 1ull << k;
     }
     if (mine) atomicOr(&s_mask, mine);
@@ -140,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
         if (any) {
             const BodyDev &B = P.bodies[sc.body_off + k];
             for (int t = 0; t < nb; ++t) {
-                const int32_t b = P.bnbr[(int64_t)t * P.NF + i];
+                const int32_t b = P.bnbr[list_at<T>(NF, i, t, c.s)];
                 if (P.bbody_s[b] != k) continue;
                 const float4 pb = P.bpos_s[b];
                 const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
@@ -156,12 +141,12 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
         }
         for (int a = 0; a < 6; ++a) {
             double t = any ? block_sum_d(f[a], sh) : 0.0;
-            if (threadIdx.x == 0) P.body_partial[((int64_t)(sc.body_off + k) * 6 + a) * P.nfblk + blockIdx.x] = t;
+            if (threadIdx.x == 0) P.body_partial[((int64_t)(sc.body_off + k) * 6 + a) * P.ntblk + blockIdx.x] = t;
         }
     }
 }
 
-// Sum of one body's force or torque component over its scene's fluid blocks, in block
+// Sum of one body's force or torque component over its scene's sweep blocks, in block
 // order (one CUDA block per body and component).
 __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
 {
@@ -170,10 +155,10 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
     const int body = blockIdx.x / 6, a = blockIdx.x % 6;
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];
-    const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.nfblk + sc.fblk_first;
+    const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first;
     double t = 0.0;
 #pragma unroll 4
-    for (int q = threadIdx.x; q < sc.fblk_count; q += 256) t += part[q];
+    for (int q = threadIdx.x; q < sc.tblk_count; q += 256) t += part[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
@@ -198,7 +183,10 @@ void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s)
 }
 void launch_body_force(const Ptrs &P, cudaStream_t s)
 {
-    if (P.nfblk) k_body_force<<<P.nfblk, kBlock, 0, s>>>(P);
+    if (!P.ntblk) return;
+#define SPH_L(T) k_body_force<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
 }
 void launch_body_reduce(const Ptrs &P, cudaStream_t s)
 {

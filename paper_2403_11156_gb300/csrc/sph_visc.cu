@@ -8,20 +8,11 @@
 // keeps rho so that one gather serves both.  Dot products are accumulated per block in
 // FP64 and reduced in a fixed order by the last block of each scene; the loop runs on the
 // device (CUDA graph while node) until |r| <= tol |b| or cg_max_iter.
-#include "sph_internal.cuh"
+#include "sph_sweep.cuh"
 
 namespace sph {
 
 namespace {
-
-__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
-{
-    if (!(r2 > 0.0f)) return 0.0f;
-    float rinv = rsqrtf(r2);
-    float q = r2 * rinv * sc.inv_h;
-    float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
-    return sc.kgrad * g * rinv;
-}
 
 struct Ctx {
     const SceneDev *sc;
@@ -42,27 +33,30 @@ __device__ __forceinline__ Ctx ctx(const Ptrs &P)
     return c;
 }
 
-// y = (I - dt A) x at particle i; X holds x in xyz and rho in w.
-__device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, int64_t i, float4 pi, float4 xi,
-                                          const float4 *__restrict__ X, float dt)
+// y = (I - dt A) x at particle i from T lanes (every thread of the warp calls it; the
+// result is valid in lanes of valid particles); X holds x in xyz and rho in w.
+template <int T>
+__device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, const Lane<T> &c, float4 pi,
+                                          float4 xi, const float4 *__restrict__ X, float dt)
 {
-    const int64_t NF = P.NF;
-    const int nn = P.nnf[i];
+    const int64_t NF = P.NF, i = c.i;
     const float reg = 0.01f * sc.h2;
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    for (int k = 0; k < nn; ++k) {
-        const int32_t j = __ldg(P.nbr + (int64_t)k * NF + i);
-        const float4 pj = __ldg(P.pos_s + j);
-        const float4 xj = __ldg(X + j);
-        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        // grad W_ij (x_ij . (x_j - x_i)) / (rho_j (r^2 + reg))
-        const float s = grad_factor(sc, r2) * (dx * (xj.x - xi.x) + dy * (xj.y - xi.y) + dz * (xj.z - xi.z)) /
-                        (xj.w * (r2 + reg));
-        ax = fmaf(s, dx, ax); ay = fmaf(s, dy, ay); az = fmaf(s, dz, az);
+    if (c.valid) {
+        for_list<4, T>(P.nbr, NF, i, c.s, lane_count<T>(P.nnf[i], c.s), [&](int32_t j) {
+            const float4 pj = __ldg(P.pos_s + j);
+            const float4 xj = __ldg(X + j);
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            // grad W_ij (x_ij . (x_j - x_i)) / (rho_j (r^2 + reg))
+            const float q = grad_factor(sc, r2) * (dx * (xj.x - xi.x) + dy * (xj.y - xi.y) + dz * (xj.z - xi.z)) /
+                            (xj.w * (r2 + reg));
+            ax = fmaf(q, dx, ax); ay = fmaf(q, dy, ay); az = fmaf(q, dz, az);
+        });
     }
+    ax = group_sum<T>(ax); ay = group_sum<T>(ay); az = group_sum<T>(az);
     // (A x)_i = -10 mu m / rho_i * acc, so (I - dt A) x = x + dt 10 mu m / rho_i * acc
-    const float k = dt * 10.0f * sc.mu * sc.m / xi.w;
+    const float k = c.valid ? dt * 10.0f * sc.mu * sc.m / xi.w : 0.0f;
     return make_float3(fmaf(k, ax, xi.x), fmaf(k, ay, xi.y), fmaf(k, az, xi.z));
 }
 
@@ -96,9 +90,10 @@ __device__ void block_sum2(double &a, double &b, double *sh)
     }
 }
 
-// Per-block partial sums, then the scene's last block sums them in block order.  Returns
-// true in thread 0 of the last block, with the totals in a and b.
-__device__ bool scene_reduce2(const Ptrs &P, const SceneDev &sc, SceneState &st, double &a, double &b,
+// Per-block partial sums, then the scene's last block sums them in block order (the
+// scene's blocks are [first, first + count) of the launch).  Returns true in thread 0 of
+// the last block, with the totals in a and b.
+__device__ bool scene_reduce2(const Ptrs &P, int32_t first, int32_t count, SceneState &st, double &a, double &b,
                               double *sh, int *s_last)
 {
     block_sum2(a, b, sh);
@@ -107,16 +102,18 @@ __device__ bool scene_reduce2(const Ptrs &P, const SceneDev &sc, SceneState &st,
         P.cg_dots[2 * blockIdx.x + 1] = b;
         __threadfence();
         uint32_t prev = atomicAdd(&st.counter, 1u);
-        *s_last = (prev == (uint32_t)sc.fblk_count - 1u);
+        *s_last = (prev == (uint32_t)count - 1u);
     }
     __syncthreads();
     if (!*s_last) return false;
     __threadfence();
-    const volatile double *d = P.cg_dots;
+    const double2 *d = reinterpret_cast<const double2 *>(P.cg_dots) + first;
     double ta = 0.0, tb = 0.0;
-    for (int k = threadIdx.x; k < sc.fblk_count; k += kBlock) {
-        ta += d[2 * (sc.fblk_first + k)];
-        tb += d[2 * (sc.fblk_first + k) + 1];
+#pragma unroll 8
+    for (int k = threadIdx.x; k < count; k += kBlock) {
+        const double2 v = __ldcg(d + k);
+        ta += v.x;
+        tb += v.y;
     }
     block_sum2(ta, tb, sh);
     a = ta;
@@ -131,28 +128,29 @@ __device__ __forceinline__ bool cg_active(const SceneDev &sc, const SceneState &
 }
 
 // x0 = v~ (already in vel_c), r0 = b - (I - dt A) x0, p0 = r0; |r0|^2 and |b|^2.
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
     __shared__ int s_last;
     kernel_enter(P.ctl, KID_CG_INIT);
-    Ctx c = ctx(P);
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
-    if (sc.visc_mode != 3) return;
+    if (sc.visc_mode != 3) return;  // uniform per block
     double rr = 0.0, bb = 0.0;
-    if (c.valid) {
-        const int64_t i = c.i;
-        const float4 pi = P.pos_s[i];
-        const float4 xi = P.vel_c[i];
-        const float3 mx = apply_m(P, sc, i, pi, xi, P.vel_c, st.dt);
+    const int64_t i = c.i;
+    const float4 pi = c.valid ? P.pos_s[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xi = c.valid ? P.vel_c[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float3 mx = apply_m<T>(P, sc, c, pi, xi, P.vel_c, st.dt);
+    if (c.valid && c.s == 0) {
         const float4 r = make_float4(xi.x - mx.x, xi.y - mx.y, xi.z - mx.z, xi.w);
         P.cg_r[i] = r;
         P.cg_p[i] = r;
         rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
         bb = (double)xi.x * xi.x + (double)xi.y * xi.y + (double)xi.z * xi.z;
     }
-    if (scene_reduce2(P, sc, st, rr, bb, sh, &s_last)) {
+    if (scene_reduce2(P, sc.tblk_first, sc.tblk_count, st, rr, bb, sh, &s_last)) {
         st.cg_rr = rr;
         st.cg_bb = bb;
         st.cg_it = 0;
@@ -163,25 +161,27 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
 }
 
 // Ap = (I - dt A) p; alpha = |r|^2 / p.Ap.
+template <int T>
 __global__ void __launch_bounds__(kBlock) k_cg_ap(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
     __shared__ int s_last;
     kernel_enter(P.ctl, KID_CG_AP);
-    Ctx c = ctx(P);
+    const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
-    if (!cg_active(sc, st)) return;
+    if (!cg_active(sc, st)) return;  // uniform per block
     double pap = 0.0, unused = 0.0;
-    if (c.valid) {
-        const int64_t i = c.i;
-        const float4 pi = P.pos_s[i];
-        const float4 p = P.cg_p[i];
-        const float3 ap = apply_m(P, sc, i, pi, p, P.cg_p, st.dt);
+    const int64_t i = c.i;
+    const float4 pi = c.valid ? P.pos_s[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 p = c.valid ? P.cg_p[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float3 ap = apply_m<T>(P, sc, c, pi, p, P.cg_p, st.dt);
+    if (c.valid && c.s == 0) {
         P.cg_ap[i] = make_float4(ap.x, ap.y, ap.z, 0.0f);
         pap = (double)p.x * ap.x + (double)p.y * ap.y + (double)p.z * ap.z;
     }
-    if (scene_reduce2(P, sc, st, pap, unused, sh, &s_last)) st.cg_alpha = pap > 0.0 ? st.cg_rr / pap : 0.0;
+    if (scene_reduce2(P, sc.tblk_first, sc.tblk_count, st, pap, unused, sh, &s_last))
+        st.cg_alpha = pap > 0.0 ? st.cg_rr / pap : 0.0;
 }
 
 // x += alpha p, r -= alpha Ap; beta = |r_new|^2 / |r|^2.
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
         P.cg_r[i] = r;
         rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
     }
-    if (scene_reduce2(P, sc, st, rr, unused, sh, &s_last)) {
+    if (scene_reduce2(P, sc.fblk_first, sc.fblk_count, st, rr, unused, sh, &s_last)) {
         st.cg_beta = st.cg_rr > 0.0 ? rr / st.cg_rr : 0.0;
         st.cg_rr = rr;
         st.cg_it += 1;
@@ -264,8 +264,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P, cudaGraphConditionalHan
 
 }  // namespace
 
-void launch_cg_init(const Ptrs &P, cudaStream_t s) { k_cg_init<<<P.nfblk, kBlock, 0, s>>>(P); }
-void launch_cg_ap(const Ptrs &P, cudaStream_t s) { k_cg_ap<<<P.nfblk, kBlock, 0, s>>>(P); }
+void launch_cg_init(const Ptrs &P, cudaStream_t s)
+{
+#define SPH_L(T) k_cg_init<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
+void launch_cg_ap(const Ptrs &P, cudaStream_t s)
+{
+#define SPH_L(T) k_cg_ap<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
 void launch_cg_xr(const Ptrs &P, cudaStream_t s) { k_cg_xr<<<P.nfblk, kBlock, 0, s>>>(P); }
 void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
 {

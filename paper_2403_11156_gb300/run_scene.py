@@ -5,7 +5,8 @@
 Workloads: small (8k-particle dam break), rigid (1.2M-particle dam break with rigid boxes),
 column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k particles).
 --eager launches the kernels one by one (the form a kernel profiler can attribute);
-without it a step is one CUDA-graph launch.
+without it a step is one CUDA-graph launch.  --lanes sets the threads per particle of the
+neighbour sweeps (1, 2, 4; 0 chooses by size).
 """
 from __future__ import annotations
 
@@ -29,9 +30,12 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--eager", action="store_true")
     ap.add_argument("--dt", type=float, default=0.0)
+    ap.add_argument("--lanes", type=int, default=0, help="threads per particle (0: by size)")
     args = ap.parse_args()
     build.build()
     descs = WORKLOADS[args.scene]()
+    for d in descs:
+        d["lanes_per_particle"] = args.lanes
     g = sph.Context(descs, torch_allocator=False)
     g.sph_set_mode(graph=not args.eager, timing=False)
     t = time.perf_counter()

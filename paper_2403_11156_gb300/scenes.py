@@ -30,7 +30,7 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
            max_iter_density=100, min_iter_divergence=1, max_iter_divergence=100,
            viscosity_mode=VISC_EXPLICIT, warm_start=WARM_PREVIOUS, divergence_solve=1,
            xsph_c=0.0, cg_tol=1e-4, cg_max_iter=500, max_fluid_neighbors=0,
-           max_boundary_neighbors=0, cell_size=0.0):
+           max_boundary_neighbors=0, cell_size=0.0, lanes_per_particle=0):
     return dict(radius=float(radius), rest_density=float(rest_density),
                 viscosity=float(viscosity), gravity=tuple(float(g) for g in gravity),
                 domain_min=tuple(float(a) for a in domain_min),
@@ -45,7 +45,7 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
                 cg_tol=float(cg_tol), cg_max_iter=int(cg_max_iter),
                 max_fluid_neighbors=int(max_fluid_neighbors),
                 max_boundary_neighbors=int(max_boundary_neighbors),
-                cell_size=float(cell_size))
+                cell_size=float(cell_size), lanes_per_particle=int(lanes_per_particle))
 
 
 def lattice_block(n, spacing, origin, jitter=0.0, rng=None):

@@ -75,6 +75,7 @@ class SceneDesc(C.Structure):
         ("viscosity_mode", C.c_int32), ("warm_start", C.c_int32),
         ("divergence_solve", C.c_int32), ("max_fluid_neighbors", C.c_int32),
         ("max_boundary_neighbors", C.c_int32), ("cg_tol", C.c_float), ("cg_max_iter", C.c_int32),
+        ("lanes_per_particle", C.c_int32),
     ]
 
 
@@ -97,14 +98,15 @@ class Tuning(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("from_cache", C.c_int32), ("gather_batch", C.c_int32),
                 ("cell_factor", C.c_float), ("n_trials", C.c_int32),
                 ("trial_cell_factor", C.c_float * 8), ("trial_batch", C.c_int32 * 8),
-                ("trial_ms", C.c_float * 8)]
+                ("trial_ms", C.c_float * 8), ("lanes", C.c_int32), ("trial_lanes", C.c_int32 * 8)]
 
     def as_dict(self):
         n = self.n_trials
         return {"tuned": self.tuned, "from_cache": self.from_cache, "gather_batch": self.gather_batch,
-                "cell_factor": self.cell_factor,
+                "cell_factor": self.cell_factor, "lanes": self.lanes,
                 "trials": [{"cell_factor": self.trial_cell_factor[k], "gather_batch": self.trial_batch[k],
-                            "ms_per_step": self.trial_ms[k]} for k in range(n)]}
+                            "lanes": self.trial_lanes[k], "ms_per_step": self.trial_ms[k]}
+                           for k in range(n)]}
 
 
 class KernelTime(C.Structure):
@@ -250,6 +252,7 @@ def _make_desc(d, keep):
     s.max_boundary_neighbors = d.get("max_boundary_neighbors", 0)
     s.cg_tol = d.get("cg_tol", 1e-4)
     s.cg_max_iter = d.get("cg_max_iter", 500)
+    s.lanes_per_particle = d.get("lanes_per_particle", 0)
     return s
 
 

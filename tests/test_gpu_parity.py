@@ -2,6 +2,8 @@
 seeded inputs.
 
 Bit-exact: cell keys, (key, id) sort order, fluid and boundary neighbour counts.
+Every check runs with 1, 2 and 4 threads per particle in the neighbour sweeps (the
+neighbour sets are the same; only the FP32 summation order changes).
 FP32 vs FP64 fields from one step off identical states with the iteration counts forced
 equal: density, Psi and alpha within 1e-5 relative (alpha with a floor of 1e-3 rms for
 free-surface particles whose factor is tiny); the stiffnesses kappa within 1e-5 of their
@@ -33,9 +35,13 @@ def _small(**kw):
     return scenes.dam_break_small(seed=7, n=(9, 11, 13), box=0.4, **kw)
 
 
+LANES = [1, 2, 4]
+
+
+@pytest.mark.parametrize("lanes", LANES)
 @pytest.mark.parametrize("make", [_small, _c1])
-def test_neighbor_structures_bit_exact(make):
-    d = forced(make(), 1, 2)
+def test_neighbor_structures_bit_exact(make, lanes):
+    d = forced(make(lanes_per_particle=lanes), 1, 2)
     g = gpu_ctx(d)
     g.sph_step(DT)
     g.sph_synchronize(raise_on_error=False)
@@ -55,12 +61,13 @@ def test_neighbor_structures_bit_exact(make):
                                   oracle.neighbor_counts_brute(x, d["boundary_x"], h, False))
 
 
-def test_exact_lattice_ties():
+@pytest.mark.parametrize("lanes", LANES)
+def test_exact_lattice_ties(lanes):
     # positions exact in float, spacing h/2: pairs at exactly h are excluded by '<'
     r = 2.0 ** -7
     x = scenes.lattice_block((10, 10, 10), 2 * r, (0.25, 0.25, 0.25))
     d = scenes.random_cloud(1, radius=r, extent=0.6, gravity=(0, 0, 0), warm_start=0,
-                            max_iter_density=0, max_iter_divergence=0)
+                            max_iter_density=0, max_iter_divergence=0, lanes_per_particle=lanes)
     d["fluid_x"], d["fluid_v"] = x, np.zeros_like(x)
     g = gpu_ctx(d)
     g.sph_step(DT)
@@ -69,9 +76,10 @@ def test_exact_lattice_ties():
     assert nn[5 + 10 * (5 + 10 * 5)] == 26
 
 
+@pytest.mark.parametrize("lanes", LANES)
 @pytest.mark.parametrize("make", [_small, _c1])
-def test_density_alpha_psi(make):
-    d = forced(make(), 1, 2)
+def test_density_alpha_psi(make, lanes):
+    d = forced(make(lanes_per_particle=lanes), 1, 2)
     g = gpu_ctx(d)
     g.sph_step(DT)
     o = oracle_step(d, DT)
@@ -98,10 +106,11 @@ def _assert_abs(gpu, ref, tol, what):
         what, e.max(), k, gpu[k], ref[k], tol[k])
 
 
+@pytest.mark.parametrize("lanes", LANES)
 @pytest.mark.parametrize("make,warm,visc", [
     (_small, 0, 1), (_small, 1, 1), (_c1, 1, 1), (_small, 1, 2), (_small, 1, 0)])
-def test_one_step_fields(make, warm, visc):
-    d = forced(make(warm_start=warm, viscosity_mode=visc, xsph_c=0.05), 2, 3)
+def test_one_step_fields(make, warm, visc, lanes):
+    d = forced(make(warm_start=warm, viscosity_mode=visc, xsph_c=0.05, lanes_per_particle=lanes), 2, 3)
     g = gpu_ctx(d)
     o = oracle.Scene(d)
     # a first step builds the warm-start memory on both sides from the same input; the

@@ -19,10 +19,11 @@ def _scene():
     return scenes.dam_break_rigid(seed=9, n=(30, 22, 22), tank=(0.5, 0.25, 0.35), box_edge=0.04)
 
 
-def _submerged():
+def _submerged(lanes=1):
     """The small scene with its boxes moved into the fluid block (fluid particles inside
     a box, or within one spacing of its surface, removed) so the coupling is active."""
     d = forced(_scene(), 2, 3)
+    d["lanes_per_particle"] = lanes
     bx = d["boundary_x"].copy()
     keep = np.ones(len(d["fluid_x"]), bool)
     for k, b in enumerate(d["bodies"]):
@@ -38,8 +39,9 @@ def _submerged():
     return d
 
 
-def test_body_force_and_update():
-    d = _submerged()
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_body_force_and_update(lanes):
+    d = _submerged(lanes)
     dt = 5e-4
     g = gpu_ctx(d)
     o = oracle.Scene(d)

@@ -28,11 +28,31 @@ def test_noconverge_reported_and_state_advances():
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK   # already reported
 
 
-def test_overflow_reported():
-    g = gpu_ctx(_small(max_fluid_neighbors=8))
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_overflow_reported(lanes):
+    g = gpu_ctx(_small(max_fluid_neighbors=8, lanes_per_particle=lanes))
     g.sph_step(DT)
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_EOVERFLOW
     assert g.sph_get_stats()["max_fluid_nbrs"] > 8
+
+
+def test_lanes_default_by_size():
+    assert gpu_ctx(_small()).sph_get_tuning()["lanes"] == 4            # 1,287 particles
+    big = scenes.dam_break_small(n=(60, 40, 40), box=1.4)               # 96,000
+    assert gpu_ctx(big).sph_get_tuning()["lanes"] == 2
+    assert gpu_ctx(dict(big, lanes_per_particle=1)).sph_get_tuning()["lanes"] == 1
+
+
+def test_lanes_change_only_rounding():
+    # the same 10 steps with 1 and 4 threads per particle: identical neighbour counts,
+    # iteration counts equal or off by one, positions within FP32 rounding growth
+    a, b = gpu_ctx(_small(lanes_per_particle=1)), gpu_ctx(_small(lanes_per_particle=4))
+    for g in (a, b):
+        g.sph_steps(10, DT)
+    np.testing.assert_array_equal(a.sph_read_field(sph.FIELD_NN_FLUID), b.sph_read_field(sph.FIELD_NN_FLUID))
+    sa, sb = a.sph_get_stats(), b.sph_get_stats()
+    assert abs(sa["total_dens_iters"] - sb["total_dens_iters"]) <= 2
+    np.testing.assert_allclose(a.sph_read_state()[0], b.sph_read_state()[0], rtol=0, atol=1e-5)
 
 
 def test_checkpoint_resume_bit_exact():

@@ -1,7 +1,9 @@
 """Autotuner and the 125-cell stencil: with cells of h/2 (1 + 2^-8) the grid keys, the
 (key, id) order and the neighbour counts stay bit-exact against the oracle's contracts
 (the oracle's key function takes the cell size as a parameter), density and alpha stay
-within 1e-5; autotuning times four candidates, keeps the fastest and caches it."""
+within 1e-5; autotuning times eight candidates (two cell sizes times (threads per
+particle, gather batch) in (1, 4), (1, 8), (2, 4), (4, 4)), keeps the fastest and caches
+it; lanes_per_particle given by the caller stays fixed."""
 import numpy as np
 import pytest
 
@@ -38,13 +40,22 @@ def test_autotune_picks_fastest_and_caches():
     d = scenes.dam_break_small(seed=9)
     g = gpu_ctx(d, autotune=True)
     t = g.sph_get_tuning()
-    assert t["tuned"] == 1 and t["from_cache"] == 0 and len(t["trials"]) == 4
+    assert t["tuned"] == 1 and t["from_cache"] == 0 and len(t["trials"]) == 8
+    assert sorted({(r["lanes"], r["gather_batch"]) for r in t["trials"]}) == [(1, 4), (1, 8), (2, 4), (4, 4)]
     best = min(t["trials"], key=lambda r: r["ms_per_step"])
     assert t["gather_batch"] == best["gather_batch"] and t["cell_factor"] == pytest.approx(best["cell_factor"])
+    assert t["lanes"] == best["lanes"]
     g.sph_steps(20, 0.0)
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
     st = g.sph_get_stats()
     assert st["dens_err"] <= 1e-3 and st["flags"] == 0
     g2 = gpu_ctx(d, autotune=True)
     t2 = g2.sph_get_tuning()
-    assert t2["from_cache"] == 1 and t2["gather_batch"] == t["gather_batch"]
+    assert t2["from_cache"] == 1 and t2["gather_batch"] == t["gather_batch"] and t2["lanes"] == t["lanes"]
+
+
+def test_autotune_keeps_given_lanes():
+    d = scenes.dam_break_small(seed=10, n=(12, 10, 10), lanes_per_particle=2)
+    t = gpu_ctx(d, autotune=True).sph_get_tuning()
+    assert t["lanes"] == 2 and len(t["trials"]) == 2
+    assert all(r["lanes"] == 2 for r in t["trials"])

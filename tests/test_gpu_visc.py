@@ -21,9 +21,9 @@ def _column(**kw):
     return scenes.viscous_column(**base)
 
 
-@pytest.mark.parametrize("tol", [1e-4, 1e-6])
-def test_cg_solves_oracle_system(tol):
-    d = _column(cg_tol=tol, cg_max_iter=1000)
+@pytest.mark.parametrize("tol,lanes", [(1e-4, 1), (1e-6, 1), (1e-6, 2), (1e-6, 4)])
+def test_cg_solves_oracle_system(tol, lanes):
+    d = _column(cg_tol=tol, cg_max_iter=1000, lanes_per_particle=lanes)
     rng = np.random.default_rng(1)
     d["fluid_v"] = (0.3 * rng.normal(size=d["fluid_x"].shape)).astype(np.float32)
     dt = 1e-3
