@@ -42,6 +42,11 @@ ALGO_BYTES = {
     "warm_density": 48,                         # x, v*, rho, kappa_prev -> kappa0, kappa_sum, kappa/rho
 }
 BOUNDARY_BYTES = 16                             # x_b, Psi_b per boundary particle and sweep
+# DRAM bytes (read + write) per launch measured by ncu on this workload at 1 thread per
+# particle, gather batch 4 and cell size h (1 + 2^-8), for the kernels as they are built
+# now (the roofline's `traffic`; null for any other kernel or configuration).
+TRAFFIC = {("dens_pass_a", 1, 4, 27): 211.66e6 + 16.76e6,
+           ("density_alpha", 1, 4, 27): 89.61e6 + 192.25e6}
 # FP32 operations per neighbour pair in the list sweeps (distance, spline gradient, dot)
 FLOPS_PER_PAIR = {"dens_pass_a": 26, "div_pass_a": 24, "dens_pass_b": 22, "div_pass_b": 22,
                   "dens_warm_pass_b": 22, "div_warm_pass_b": 22, "nonpressure": 30,
@@ -315,7 +320,9 @@ def main():
     achieved_gbs = algo / per_launch_s / 1e9
     nbr = float(it1["max_fluid_nbrs"])
     roof = {"kernel": name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": achieved_gbs / hbm, "traffic": None,
+            "frac": achieved_gbs / hbm,
+            "traffic": TRAFFIC.get((name, tuning.get("lanes"), tuning.get("gather_batch"),
+                                    27 if float(tuning.get("cell_factor", 0.0)) > 0.75 else 125)),
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured" else "fallback 6.8 TB/s",
             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
             "share_of_step": k_ms / total_ms if total_ms else None}
