@@ -100,13 +100,11 @@ typedef struct sph_scene_desc {
     float cg_tol;                 /* relative residual of the implicit viscosity CG   */
     int32_t cg_max_iter;
     int32_t lanes_per_particle;   /* threads per fluid particle in the neighbour      */
-                                  /* sweeps: 1, 2 or 4; 0 = by size (4 up to 77,824   */
-                                  /* fluid particles in the context, 2 up to twice    */
-                                  /* that, else 1).  Each lane keeps its own          */
-                                  /* neighbour sub-list of ceil(1.5 cap / lanes)      */
-                                  /* entries (cap for 1 lane); 4 lanes need           */
-                                  /* max_*_neighbors <= 680.  A batch uses the largest */
-                                  /* value given by its scenes.                       */
+                                  /* sweeps: 1, 2 or 4 (they share the particle's     */
+                                  /* list); 0 = by size (4 up to 77,824 fluid         */
+                                  /* particles in the context, 2 up to twice that,    */
+                                  /* else 1).  A batch uses the largest value given   */
+                                  /* by its scenes.                                   */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

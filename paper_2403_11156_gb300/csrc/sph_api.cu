@@ -20,16 +20,7 @@ namespace {
 
 constexpr int kDefaultCapF = 96;
 constexpr int kDefaultCapB = 64;
-constexpr int kDefaultLanes = 1;
 constexpr int64_t kAutoLaneThreads = 152 * 2048;  // resident threads of a full GB300
-
-// Capacity of one lane's sub-list: with T > 1 lanes a particle's neighbours are dealt to
-// the lanes by candidate index, so each sub-list gets half again its even share.
-int lane_cap(int cap, int lanes)
-{
-    return lanes == 1 ? cap : std::min(cap, (3 * cap + 2 * lanes - 1) / (2 * lanes));
-}
-int lanes_of(const sph_scene_desc &d) { return d.lanes_per_particle > 0 ? d.lanes_per_particle : kDefaultLanes; }
 constexpr double kPi = 3.14159265358979323846;
 
 struct Alloc {
@@ -173,13 +164,6 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
-    {
-        const int L = lanes_of(d);
-        const int cf = d.max_fluid_neighbors > 0 ? d.max_fluid_neighbors : kDefaultCapF;
-        const int cb = d.max_boundary_neighbors > 0 ? d.max_boundary_neighbors : kDefaultCapB;
-        if (L > 1 && (lane_cap(cf, L) >= (1 << (32 / L)) || lane_cap(cb, L) >= (1 << (32 / L))))
-            return bad("max_*_neighbors too large for 4 lanes per particle (at most 680)");
-    }
     if (d.cell_size > 0.0f && !(d.cell_size >= half_cell(d.radius))) return bad("cell_size below h/2 (1 + 2^-8)");
     if (!std::isfinite(d.cell_size)) return bad("cell_size not finite");
     if (d.n_bodies < 0 || d.n_bodies > SPH_MAX_BODIES) return bad("n_bodies out of range");
@@ -237,8 +221,8 @@ __global__ void k_read_fluid(Ptrs P, int scene, int field, void *out)
     case SPH_FIELD_ALPHA: ((float *)out)[P.id_s[i]] = P.alpha[i]; break;
     case SPH_FIELD_KAPPA: ((float *)out)[P.id_s[i]] = P.ksum[i]; break;
     case SPH_FIELD_KAPPA_V: ((float *)out)[P.id_s[i]] = P.kvsum[i]; break;
-    case SPH_FIELD_NN_FLUID: ((int32_t *)out)[P.id_s[i]] = nn_total(P.nnf[i], P.lanes); break;
-    case SPH_FIELD_NN_BOUNDARY: ((int32_t *)out)[P.id_s[i]] = nn_total(P.nnb[i], P.lanes); break;
+    case SPH_FIELD_NN_FLUID: ((int32_t *)out)[P.id_s[i]] = P.nnf[i]; break;
+    case SPH_FIELD_NN_BOUNDARY: ((int32_t *)out)[P.id_s[i]] = P.nnb[i]; break;
     case SPH_FIELD_V_DIV: {
         float4 v = P.vel_s[i];
         float *o = (float *)out + 3 * P.id_s[i];
@@ -556,23 +540,17 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     c->scenes.resize(n);
     int64_t NF = 0, NB = 0, NC = 0;
     int32_t nfblk = 0, nbblk = 0, ntblk = 0, nbodies = 0;
-    int lcap_f = 0, lcap_b = 0;
+    int cap_f = 0, cap_b = 0;
     // threads per particle in the neighbour sweeps: one value for the whole context, the
     // largest one given, else by size: enough threads to fill every SM (4 lanes below
-    // 152 x 2048 / 4 particles, 2 below twice that), as far as the list capacities allow
+    // 152 x 2048 / 4 particles, 2 below twice that)
     int lanes = 0;
     for (int s = 0; s < n; ++s) lanes = std::max(lanes, (int)descs[s].lanes_per_particle);
     if (lanes == 0) {
         int64_t nf = 0;
-        int cap = 0;
-        for (int s = 0; s < n; ++s) {
-            nf += descs[s].n_fluid;
-            cap = std::max(cap, descs[s].max_fluid_neighbors > 0 ? descs[s].max_fluid_neighbors : kDefaultCapF);
-            cap = std::max(cap, descs[s].max_boundary_neighbors > 0 ? descs[s].max_boundary_neighbors : kDefaultCapB);
-        }
+        for (int s = 0; s < n; ++s) nf += descs[s].n_fluid;
         const int64_t fill = kAutoLaneThreads;
         lanes = nf * 4 <= fill ? 4 : (nf * 2 <= fill ? 2 : 1);
-        while (lanes > 1 && lane_cap(cap, lanes) >= (1 << (32 / lanes))) lanes /= 2;
     }
     for (int s = 0; s < n; ++s) {
         const sph_scene_desc &d = descs[s];
@@ -629,14 +607,20 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.tblk_count = (int32_t)((d.n_fluid * lanes + kBlock - 1) / kBlock);
         q.cap_f = d.max_fluid_neighbors > 0 ? d.max_fluid_neighbors : kDefaultCapF;
         q.cap_b = d.max_boundary_neighbors > 0 ? d.max_boundary_neighbors : kDefaultCapB;
-        q.lcap_f = lane_cap(q.cap_f, lanes);
-        q.lcap_b = lane_cap(q.cap_b, lanes);
+        {
+            // stencil culling margin: 1e-3 h, plus a bound on the rounding of cell bounds and
+            // coordinates of the domain's magnitude (a few float ulps)
+            double mag = 0.0;
+            for (int a = 0; a < 3; ++a)
+                mag = std::max(mag, std::max(std::fabs((double)d.domain_min[a]), std::fabs((double)d.domain_max[a])));
+            mag += 2.0 * q.cell;
+            const double margin = 1e-3 * h + 1e-6 * mag;
+            q.cull2 = (float)((h + margin) * (h + margin));
+        }
         q.cg_tol = d.cg_tol > 0.0f ? d.cg_tol : 1e-4f;
         q.cg_max = d.cg_max_iter > 0 ? d.cg_max_iter : 500;
-        if (lanes > 1 && (q.lcap_f >= (1 << (32 / lanes)) || q.lcap_b >= (1 << (32 / lanes))))
-            return bail(fail(c, SPH_EINVAL, "scene %d: max_*_neighbors too large for %d lanes per particle", s, lanes));
-        lcap_f = std::max(lcap_f, q.lcap_f);
-        lcap_b = std::max(lcap_b, q.lcap_b);
+        cap_f = std::max(cap_f, q.cap_f);
+        cap_b = std::max(cap_b, q.cap_b);
         for (int k = 0; k < q.fblk_count; ++k) c->fblk_scene.push_back(s);
         for (int k = 0; k < q.bblk_count; ++k) c->bblk_scene.push_back(s);
         for (int k = 0; k < q.tblk_count; ++k) c->tblk_scene.push_back(s);
@@ -656,7 +640,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         c->any_learned |= d.warm_start == 2;
         c->any_implicit |= d.viscosity_mode == 3;
     }
-    if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * lanes * lcap_f > 4.0e10)
+    if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * cap_f > 4.0e10)
         return bail(fail(c, SPH_EINVAL, "context too large"));
     Ptrs &P = c->P;
     P.nfblk = nfblk;
@@ -685,7 +669,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
           dalloc(c, P.kvprev_s, NF);
     ok &= dalloc(c, P.ksum, NF) && dalloc(c, P.kvsum, NF) && dalloc(c, P.alpha, NF) && dalloc(c, P.k0, NF);
     ok &= dalloc(c, P.id_c, NF) && dalloc(c, P.id_s, NF) && dalloc(c, P.nnf, NF) && dalloc(c, P.nnb, NF);
-    ok &= dalloc(c, P.nbr, (size_t)NF * lanes * lcap_f) && dalloc(c, P.bnbr, (size_t)NF * lanes * lcap_b);
+    ok &= dalloc(c, P.nbr, (size_t)NF * cap_f) && dalloc(c, P.bnbr, (size_t)NF * cap_b);
     ok &= dalloc(c, P.feat, (size_t)NF * 4);
     ok &= dalloc(c, P.cell_count, NC) && dalloc(c, P.cell_start, NC + 1);
     ok &= dalloc(c, P.key_tmp, NF) && dalloc(c, P.slot_tmp, NF) && dalloc(c, P.sid_tmp, NF) &&
@@ -924,13 +908,9 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
             cached = true;
         }
     }
-    // lanes given by the caller stay fixed; 4 lanes need capacities of at most 680
-    int fixed_lanes = 0, max_cap = 0;
-    for (int s = 0; s < n; ++s) {
-        fixed_lanes = std::max(fixed_lanes, (int)descs[s].lanes_per_particle);
-        max_cap = std::max(max_cap, descs[s].max_fluid_neighbors > 0 ? descs[s].max_fluid_neighbors : kDefaultCapF);
-        max_cap = std::max(max_cap, descs[s].max_boundary_neighbors > 0 ? descs[s].max_boundary_neighbors : kDefaultCapB);
-    }
+    // lanes given by the caller stay fixed
+    int fixed_lanes = 0;
+    for (int s = 0; s < n; ++s) fixed_lanes = std::max(fixed_lanes, (int)descs[s].lanes_per_particle);
     auto set_trial = [&](float factor, int lanes) {
         for (int s = 0; s < n; ++s) {
             trial[s].cell_size = descs[s].cell_size < 0.0f ? 4.0f * descs[s].radius * factor : descs[s].cell_size;
@@ -945,7 +925,6 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
         for (int f = 0; f < 2; ++f)
             for (int b = 0; b < 4; ++b) {
                 if (fixed_lanes && lanes_c[b] != fixed_lanes) continue;
-                if (lanes_c[b] == 4 && lane_cap(max_cap, 4) > 255) continue;
                 set_trial(factors[f], lanes_c[b]);
                 float ms = 0.0f;
                 sph_status st = time_config(trial, alloc, stream, batch_c[b], 5, &ms);

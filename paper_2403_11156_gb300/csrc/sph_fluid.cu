@@ -127,46 +127,94 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         const int32_t cy = cell_coord(pi.y, sc.origin[1], sc.cell, sc.dims[1]);
         const int32_t cz = cell_coord(pi.z, sc.origin[2], sc.cell, sc.dims[2]);
         const int32_t R = sc.R;
-        const int32_t x0 = max(cx - R, 0), x1 = min(cx + R, sc.dims[0] - 1);
-        const float h2 = sc.h2;
-        const int lcap_f = sc.lcap_f, lcap_b = sc.lcap_b;
-        int32_t *__restrict__ nbr = P.nbr;
-        int32_t *__restrict__ bnbr = P.bnbr;
+        const float h2 = sc.h2, cull2 = sc.cull2, cs = sc.cell;
+        // offset of the particle inside its cell, per axis: the distance from the particle
+        // to a stencil cell d cells away is at least gap(d) (zero for d = 0)
+        const float ox = pi.x - fmaf((float)cx, cs, sc.origin[0]);
+        const float oy = pi.y - fmaf((float)cy, cs, sc.origin[1]);
+        const float oz = pi.z - fmaf((float)cz, cs, sc.origin[2]);
+        auto gap = [&](float o, int32_t d) {
+            const float g = d < 0 ? fmaf((float)(-d - 1), cs, o) : (d > 0 ? fmaf((float)d, cs, -o) : 0.0f);
+            return fmaxf(g, 0.0f);
+        };
+        const int cap_f = sc.cap_f, cap_b = sc.cap_b;
+        const uint32_t self = (uint32_t)i;
+        // the group's lanes relative to this one (cooperative append for T > 1)
+        const unsigned gmask = group_mask<T>();
+        const int gshift = (int)(threadIdx.x & 31u) & ~(T - 1);
+        const unsigned below = (1u << s) - 1u;
         // phase 1: the float predicate over the stencil's index ranges only records
         // neighbours; keeping the per-pair work out of this loop keeps the warp converged
-        // while most candidates are rejected
+        // while most candidates are rejected.  Rows and end cells whose nearest point is
+        // farther than h (plus a margin above the rounding of these bounds) are skipped:
+        // they hold no particle that passes the predicate, so the lists are unchanged.
+        // With T > 1 the lanes test T consecutive candidates at a time and append the hits
+        // in candidate order (ballot over the group), so every T builds the same list.
         for (int32_t dz = -R; dz <= R; ++dz) {
             const int32_t z = cz + dz;
             if (z < 0 || z >= sc.dims[2]) continue;
+            const float gz = gap(oz, dz);
             for (int32_t dy = -R; dy <= R; ++dy) {
                 const int32_t y = cy + dy;
                 if (y < 0 || y >= sc.dims[1]) continue;
+                const float gy = gap(oy, dy);
+                const float g2 = fmaf(gy, gy, gz * gz);
+                if (g2 > cull2) continue;
+                int32_t x0 = cx - R, x1 = cx + R;
+                while (x0 < cx && fmaf(gap(ox, x0 - cx), gap(ox, x0 - cx), g2) > cull2) ++x0;
+                while (x1 > cx && fmaf(gap(ox, x1 - cx), gap(ox, x1 - cx), g2) > cull2) --x1;
+                x0 = max(x0, 0);
+                x1 = min(x1, sc.dims[0] - 1);
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
                 const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
-                for_range<4, T>(P.pos_s, jb + (uint32_t)s, je, [&](uint32_t j, float4 pj) {
-                    float dx, dy2, dz2;
-                    const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-                    if (d2 < h2 && (int64_t)j != i) {
-                        if (nn_f < lcap_f) nbr[list_at<T>(NF, i, nn_f, s)] = (int32_t)j;
-                        ++nn_f;
-                    }
-                });
-                if (sc.nb > 0) {
-                    const uint32_t bb = P.bcell_start[row + x0], be = P.bcell_start[row + x1 + 1];
-                    for_range<1, T>(P.bpos_s, bb + (uint32_t)s, be, [&](uint32_t b, float4 pb) {
+                if constexpr (T == 1) {
+                    for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
                         float dx, dy2, dz2;
-                        const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
-                        if (d2 < h2) {
-                            if (nn_b < lcap_b) bnbr[list_at<T>(NF, i, nn_b, s)] = (int32_t)b;
-                            ++nn_b;
+                        const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
+                        if (d2 < h2 && j != self) {
+                            if (nn_f < cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
+                            ++nn_f;
                         }
                     });
+                } else {
+                    for (uint32_t j0 = jb; j0 < je; j0 += (uint32_t)T) {   // uniform in the group
+                        const uint32_t j = j0 + (uint32_t)s;
+                        bool hit = false;
+                        if (j < je) {
+                            float dx, dy2, dz2;
+                            hit = pred_d2(pi, __ldg(P.pos_s + j), dx, dy2, dz2) < h2 && j != self;
+                        }
+                        const unsigned bits = __ballot_sync(gmask, hit) >> gshift;
+                        const int slot = nn_f + __popc(bits & below);
+                        if (hit && slot < cap_f) P.nbr[(int64_t)slot * NF + i] = (int32_t)j;
+                        nn_f += __popc(bits);
+                    }
+                }
+                if (sc.nb > 0) {
+                    const uint32_t bb = P.bcell_start[row + x0], be = P.bcell_start[row + x1 + 1];
+                    for (uint32_t b0 = bb; b0 < be; b0 += (uint32_t)T) {
+                        const uint32_t b = b0 + (uint32_t)s;
+                        bool hit = false;
+                        if (b < be) {
+                            float dx, dy2, dz2;
+                            hit = pred_d2(pi, __ldg(P.bpos_s + b), dx, dy2, dz2) < h2;
+                        }
+                        const unsigned bits = T == 1 ? (unsigned)hit : (__ballot_sync(gmask, hit) >> gshift);
+                        const int slot = nn_b + __popc(bits & below);
+                        if (hit && slot < cap_b) P.bnbr[(int64_t)slot * NF + i] = (int32_t)b;
+                        nn_b += __popc(bits);
+                    }
                 }
             }
         }
-        // phase 2: density, alpha and the warm-start gate over the recorded sub-list
+        // the lists were written by the group's lanes: order them before the reads below
+        if (T > 1) __syncwarp(gmask);
+        const int32_t *__restrict__ nbr = P.nbr;
+        const int32_t *__restrict__ bnbr = P.bnbr;
+        // phase 2: density, alpha and the warm-start gate over the recorded list (this
+        // lane's share of its entries)
         float w_sum = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f, div_f = 0.0f;
-        for_list<2, T, false>(nbr, NF, i, s, min(nn_f, lcap_f), [&](int32_t j) {
+        for_list<2, T, false>(nbr, NF, i, s, min(nn_f, cap_f), [&](int32_t j) {
             const float4 pj = __ldg(P.pos_s + j);
             float dx, dy2, dz2;
             const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
@@ -184,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         s1x = sc.m * fx; s1y = sc.m * fy; s1z = sc.m * fz;
         s2 *= sc.m * sc.m;
         div_l = sc.m * div_f;
-        const int nb = min(nn_b, lcap_b);
+        const int nb = min(nn_b, cap_b);
         if (nb > 0) {
             float wb = 0.0f, divb = 0.0f;
             const bool moving = sc.has_moving != 0;
@@ -211,29 +259,25 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
     s1x = group_sum<T>(s1x); s1y = group_sum<T>(s1y); s1z = group_sum<T>(s1z);
     s2 = group_sum<T>(s2);
     div_l = group_sum<T>(div_l);
-    const uint32_t pk_f = group_sum<T>(lane_pack<T>(min(nn_f, sc.lcap_f), s));
-    const uint32_t pk_b = group_sum<T>(lane_pack<T>(min(nn_b, sc.lcap_b), s));
-    const int tot_f = group_sum<T>(nn_f), tot_b = group_sum<T>(nn_b);
-    const bool lane_over = nn_f > sc.lcap_f || nn_b > sc.lcap_b;
     if (c.valid && s == 0) {
         const float rho = fmaf(sc.m, sc.sigma, rho_l);
         const float den = fmaf(s1x, s1x, fmaf(s1y, s1y, fmaf(s1z, s1z, s2)));
         const float alpha = den > sc.eps_alpha ? rho / den : 0.0f;
         P.alpha[i] = alpha;
         set_w(P.vel_s, i, rho);
-        P.nnf[i] = (int32_t)pk_f;
-        P.nnb[i] = (int32_t)pk_b;
+        P.nnf[i] = min(nn_f, sc.cap_f);
+        P.nnb[i] = min(nn_b, sc.cap_b);
         float kv0 = 0.0f;
         if (gate && div_l > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
         P.kvsum[i] = kv0;
         set_w(P.pos_s, i, kv0 / rho);
     }
-    const int mf = warp_max(tot_f), mb = warp_max(tot_b);
-    const unsigned over = __ballot_sync(0xffffffffu, lane_over);
+    // the counts are the same in all lanes of a particle
+    const int mf = warp_max(nn_f), mb = warp_max(nn_b);
     if ((threadIdx.x & 31) == 0) {
         if (mf > 0) atomicMax(&c.st->max_nn_f, mf);
         if (mb > 0) atomicMax(&c.st->max_nn_b, mb);
-        if (mf > sc.cap_f || mb > sc.cap_b || over) atomicOr(&c.st->flags, 1);
+        if (mf > sc.cap_f || mb > sc.cap_b) atomicOr(&c.st->flags, 1);
     }
 }
 
@@ -249,7 +293,7 @@ __device__ __forceinline__ float drho_dt_lane(const Ptrs &P, const SceneDev &sc,
 {
     const int64_t NF = P.NF;
     float acc = 0.0f;
-    for_list<B, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
+    for_list<B, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
         const float4 pj = __ldg(P.pos_s + j);
         const float4 vj = __ldg(V + j);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -258,7 +302,7 @@ __device__ __forceinline__ float drho_dt_lane(const Ptrs &P, const SceneDev &sc,
     });
     float accb = 0.0f;
     const bool moving = sc.has_moving != 0;
-    for_list<4, T>(P.bnbr, NF, i, s, lane_count<T>(P.nnb[i], s), [&](int32_t b) {
+    for_list<4, T>(P.bnbr, NF, i, s, P.nnb[i], [&](int32_t b) {
         const float4 pb = __ldg(P.bpos_s + b);
         const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
         const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -361,7 +405,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
         if (c.valid) {
             const float4 pi = P.pos_s[i];
             const float ki = pi.w;
-            for_list<B, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
+            for_list<B, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
                 const float4 pj = __ldg(P.pos_s + j);
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
                 const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
@@ -370,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
             ax *= sc.m; ay *= sc.m; az *= sc.m;
             if (ki != 0.0f) {
                 float bx = 0.0f, by = 0.0f, bz = 0.0f;
-                for_list<4, T>(P.bnbr, NF, i, s, lane_count<T>(P.nnb[i], s), [&](int32_t b) {
+                for_list<4, T>(P.bnbr, NF, i, s, P.nnb[i], [&](int32_t b) {
                     const float4 pb = __ldg(P.bpos_s + b);
                     const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
                     const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -446,7 +490,7 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
             const float4 pi = P.pos_s[i];
             const float reg = 0.01f * sc.h2;
             const bool lap = sc.visc_mode == 1;
-            for_list<kBatch, T>(P.nbr, NF, i, s, lane_count<T>(P.nnf[i], s), [&](int32_t j) {
+            for_list<kBatch, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
                 const float4 pj = __ldg(P.pos_s + j);
                 const float4 vj = __ldg(P.vel_s + j);
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -517,7 +561,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     float4 f;
     f.x = rho / sc.rho0 - 1.0f;
     f.y = dt * D / sc.rho0;
-    f.z = (float)(nn_total(P.nnf[i], T) + nn_total(P.nnb[i], T)) / 33.0f;
+    f.z = (float)(P.nnf[i] + P.nnb[i]) / 33.0f;
     f.w = P.kprev_s[i] / (dt * dt) / kref;
     reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;

@@ -4,8 +4,7 @@
 //   fluid, current sorted order  pos_s  float4 (x, y, z, kappa/rho of the current sweep)
 //                                vel_s  float4 (v, rho)
 //   fluid, canonical order       pos_c, vel_c (same packing), kprev_c, kvprev_c, id_c
-//   neighbour lists              nbr, bnbr: T interleaved sub-lists per particle, entry k
-//                                of sub-list s at ((k NF) + i) T + s (k-major: coalesced)
+//   neighbour lists              nbr[k * NF + i], bnbr[k * NF + i]  (k-major: coalesced)
 //   boundary, original order     bx_o float4 (x, 0), bv_o float4, br0 float4, bbody int32
 //   boundary, sorted order       bpos_s float4 (x, Psi), bvel_s float4 (v_b, 0)
 // "Canonical" is the sorted order of the previous step: the reorder gathers canonical ->
@@ -47,10 +46,10 @@ struct SceneDev {
     int32_t bblk_first, bblk_count;   // boundary particle blocks
     int32_t tblk_first, tblk_count;   // sweep blocks (kBlock / lanes particles each)
     int32_t cap_f, cap_b;             // neighbour list capacities (per particle)
-    int32_t lcap_f, lcap_b;           // capacities of one lane's sub-list
     int32_t R;                        // stencil radius in cells: 1 (cell >= h), 2 (cell >= h/2)
     float cg_tol;
     int32_t cg_max;
+    float cull2;                      // (h + margin)^2: stencil cells farther are skipped
 };
 
 // Per-scene mutable state (device).
@@ -168,7 +167,7 @@ struct Ptrs {
     float *kprev_c, *kvprev_c, *kprev_s, *kvprev_s;
     float *ksum, *kvsum, *alpha, *k0;
     int32_t *id_c, *id_s;
-    int32_t *nnf, *nnb;               // sub-list lengths, packed (32 / lanes bits each)
+    int32_t *nnf, *nnb;               // neighbour counts (capped at the list capacity)
     int32_t *nbr, *bnbr;
     float *feat;                      // [NF][4]
     // grid scratch (fluid)
@@ -212,15 +211,6 @@ __device__ __forceinline__ float pred_d2(float4 a, float4 b, float &dx, float &d
     dy = __fsub_rn(a.y, b.y);
     dz = __fsub_rn(a.z, b.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-}
-
-// Neighbour count of a particle from its packed sub-list lengths.
-__device__ __forceinline__ int32_t nn_total(int32_t packed, int32_t lanes)
-{
-    const uint32_t p = (uint32_t)packed;
-    if (lanes == 1) return (int32_t)p;
-    if (lanes == 2) return (int32_t)((p & 0xFFFFu) + (p >> 16));
-    return (int32_t)((p & 0xFFu) + ((p >> 8) & 0xFFu) + ((p >> 16) & 0xFFu) + (p >> 24));
 }
 
 enum SortWhat { SORT_FLUID = 0, SORT_BOUNDARY = 1 };

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     float kt = 0.0f;
     if (c.valid) {
-        nb = lane_count<T>(P.nnb[i], c.s);
+        nb = P.nnb[i];
         pi = P.pos_s[i];
         kt = (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
     }
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     if (threadIdx.x == 0) s_mask = 0ull;
     __syncthreads();
     unsigned long long mine = 0ull;
-    for (int t = 0; t < nb; ++t) {
-        const int32_t k = P.bbody_s[P.bnbr[list_at<T>(NF, i, t, c.s)]];
+    for (int t = c.s; t < nb; t += T) {
+        const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * NF + i]];
         if (k >= 0) mine |= 1ull << k;
     }
     if (mine) atomicOr(&s_mask, mine);
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
         const bool any = (touched >> k) & 1ull;
         if (any) {
             const BodyDev &B = P.bodies[sc.body_off + k];
-            for (int t = 0; t < nb; ++t) {
-                const int32_t b = P.bnbr[list_at<T>(NF, i, t, c.s)];
+            for (int t = c.s; t < nb; t += T) {
+                const int32_t b = P.bnbr[(int64_t)t * NF + i];
                 if (P.bbody_s[b] != k) continue;
                 const float4 pb = P.bpos_s[b];
                 const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;

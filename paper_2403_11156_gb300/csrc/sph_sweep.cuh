@@ -2,14 +2,14 @@
 // mapping of T threads ("lanes") onto one particle, and the layout of the per-step
 // neighbour lists.
 //
-// With T lanes per particle, the particle's neighbours are split into T sub-lists: lane s
-// records the candidates jb + s, jb + s + T, ... of every stencil row, and every later
-// sweep has lane s visit sub-list s, the T partial sums being combined with warp
-// shuffles.  A warp then holds 32/T consecutive particles (one or two grid cells), whose
-// k-th neighbours are nearly the same particles, so each warp-wide gather touches one or
-// two cache lines; small scenes also get T times more threads.
-// Entry k of sub-list s of particle i is at ((k NF) + i) T + s (coalesced across a warp
-// for fixed k); the T sub-list lengths are packed in one uint32 per particle, 8 bits each.
+// Entry k of particle i's list is at k NF + i (k-major: coalesced across a warp for fixed
+// k).  The T lanes of a particle share its list: lane s visits entries s, s + T, s + 2T,
+// ..., and the T partial sums are combined with warp shuffles.  A warp then holds 32/T
+// consecutive particles (about one grid cell at T = 4), whose lists are nearly the same
+// particles in the same order, so a warp-wide gather touches one or two cache lines
+// instead of four or five, and the lanes' shares differ by at most one entry.  The
+// density sweep builds each list cooperatively: the T lanes test T consecutive candidates
+// at a time and append the hits in candidate order, so the list is the same for every T.
 #pragma once
 
 #include "sph_internal.cuh"
@@ -67,49 +67,35 @@ __device__ __forceinline__ V group_sum(V v)
     return v;
 }
 
-// Sub-list lengths are packed 32/T bits each (T = 1: the plain count).
+// Mask of the T lanes of this thread's particle within its warp.
 template <int T>
-__device__ __forceinline__ uint32_t lane_mask()
+__device__ __forceinline__ unsigned group_mask()
 {
-    return T == 1 ? 0xFFFFFFFFu : ((1u << (32 / T)) - 1u);
-}
-template <int T>
-__device__ __forceinline__ int lane_count(int32_t packed, int s)
-{
-    return (int)(((uint32_t)packed >> ((32 / T) * s)) & lane_mask<T>());
-}
-template <int T>
-__device__ __forceinline__ uint32_t lane_pack(int n, int s)
-{
-    return (uint32_t)n << ((32 / T) * s);
+    return T == 32 ? 0xffffffffu : (((1u << T) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(T - 1)));
 }
 
-template <int T>
-__device__ __forceinline__ int64_t list_at(int64_t NF, int64_t i, int k, int s)
-{
-    return ((int64_t)k * NF + i) * T + s;
-}
-
-// Visit entries [0, n) of sub-list s of particle i, software-pipelined in batches of U:
-// the indices of batch b + 1 are loaded before the visits of batch b, whose U gathers the
-// compiler issues together (the visits only accumulate in registers), so each batch costs
-// one memory latency instead of two.  Prefetches past the end re-read entry n - 1.  NC:
-// the list is read-only for the kernel (read-only data path); otherwise plain loads, for
-// a list this thread has just written.  Visiting order = list order.
+// Visit this lane's entries s, s + T, ... below n of particle i's list, software-
+// pipelined in batches of U: the entries of batch b + 1 are loaded before the visits of
+// batch b, whose U gathers the compiler issues together (the visits only accumulate in
+// registers), so each batch costs one memory latency.  Prefetches past the end re-read the
+// lane's last entry.  NC: the list is read-only for the kernel (read-only data path);
+// otherwise plain loads, for a list this warp has just written.  Visiting order = list
+// order.
 template <int U, int T, bool NC = true, typename F>
 __device__ __forceinline__ void for_list(const int32_t *__restrict__ list, int64_t NF, int64_t i, int s, int n,
                                          F &&visit)
 {
-    if (n <= 0) return;
+    const int m = n > s ? (n - s + T - 1) / T : 0;   // this lane's entries
+    if (m <= 0) return;
     auto ld = [&](int k) {
-        const int64_t a = list_at<T>(NF, i, min(k, n - 1), s);
+        const int64_t a = (int64_t)(s + T * min(k, m - 1)) * NF + i;
         return NC ? __ldg(list + a) : list[a];
     };
     int32_t j[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) j[u] = ld(u);
     int k = 0;
-    for (; k + U <= n; k += U) {
+    for (; k + U <= m; k += U) {
         int32_t jn[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) jn[u] = ld(k + U + u);
@@ -120,7 +106,7 @@ __device__ __forceinline__ void for_list(const int32_t *__restrict__ list, int64
     }
 #pragma unroll
     for (int u = 0; u < U - 1; ++u)
-        if (k + u < n) visit(j[u]);
+        if (k + u < m) visit(j[u]);
 }
 
 // Visit the candidates j0, j0 + T, ... below je of a grid row in batches of U: the U

@@ -43,7 +43,7 @@ __device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, con
     const float reg = 0.01f * sc.h2;
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
     if (c.valid) {
-        for_list<4, T>(P.nbr, NF, i, c.s, lane_count<T>(P.nnf[i], c.s), [&](int32_t j) {
+        for_list<4, T>(P.nbr, NF, i, c.s, P.nnf[i], [&](int32_t j) {
             const float4 pj = __ldg(P.pos_s + j);
             const float4 xj = __ldg(X + j);
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;

@@ -46,8 +46,7 @@ def _bad(**kw):
     dict(radius=0.0), dict(rest_density=-1.0), dict(domain_max=(0.0, 0.2, 0.2)),
     dict(min_iter_density=-1), dict(max_iter_divergence=-3), dict(viscosity_mode=7), dict(warm_start=9),
     dict(dt_max=0.0), dict(max_fluid_neighbors=5000), dict(cell_size=0.01),
-    dict(lanes_per_particle=3), dict(lanes_per_particle=-1),
-    dict(lanes_per_particle=4, max_fluid_neighbors=681), dict(lanes_per_particle=4, max_boundary_neighbors=700),
+    dict(lanes_per_particle=3), dict(lanes_per_particle=-1), dict(lanes_per_particle=8),
     dict(fluid_x=np.full((3, 3), np.nan, np.float32)),
     dict(fluid_x=np.zeros((0, 3), np.float32)),
 ])
@@ -66,7 +65,7 @@ def test_accepts_good_descriptors(lib, lanes):
     import torch
     if torch.cuda.is_available():
         pytest.skip("host-only check")
-    d = _bad(lanes_per_particle=lanes, max_fluid_neighbors=680 if lanes == 4 else 0)
+    d = _bad(lanes_per_particle=lanes, max_fluid_neighbors=1024 if lanes == 4 else 0)
     with pytest.raises(sph.SphError) as e:
         sph.Context(d, torch_allocator=False)
     assert e.value.status == sph.SPH_ECUDA

@@ -76,6 +76,27 @@ def test_exact_lattice_ties(lanes):
     assert nn[5 + 10 * (5 + 10 * 5)] == 26
 
 
+@pytest.mark.parametrize("cell_factor", [1.00390625, 0.501953125])
+@pytest.mark.parametrize("lanes", LANES)
+def test_counts_with_particles_outside_domain(lanes, cell_factor):
+    # particles beyond the domain are clamped into the edge cells; the stencil culling of
+    # the density sweep must still find exactly the brute-force neighbours
+    rng = np.random.default_rng(11)
+    r = 0.01
+    x = rng.uniform(-0.06, 0.26, size=(3000, 3)).astype(np.float32)
+    d = scenes.random_cloud(1, radius=r, extent=0.2, gravity=(0, 0, 0), warm_start=0,
+                            max_iter_density=0, max_iter_divergence=0, lanes_per_particle=lanes,
+                            max_fluid_neighbors=400)
+    d["fluid_x"], d["fluid_v"] = x, np.zeros_like(x)
+    h = np.float32(4 * r)
+    d["cell_size"] = float(h * np.float32(cell_factor))
+    g = gpu_ctx(d)
+    g.sph_step(DT)
+    g.sph_synchronize(raise_on_error=False)
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_NN_FLUID),
+                                  oracle.neighbor_counts_brute(x, x, h, True))
+
+
 @pytest.mark.parametrize("lanes", LANES)
 @pytest.mark.parametrize("make", [_small, _c1])
 def test_density_alpha_psi(make, lanes):
