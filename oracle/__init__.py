@@ -54,6 +54,8 @@ class Params(C.Structure):
         ("domain_min", C.c_float * 3), ("domain_max", C.c_float * 3),
         ("xsph_c", C.c_double), ("cg_tol", C.c_double),
         ("cg_max_iter", C.c_int32), ("pad_", C.c_int32),
+        ("pressure_solver", C.c_int32), ("pad2_", C.c_int32),
+        ("eos_stiffness", C.c_double), ("eos_exponent", C.c_double),
     ]
 
 
@@ -234,6 +236,9 @@ class Scene:
         p.xsph_c = desc.get("xsph_c", 0.0)
         p.cg_tol = desc.get("cg_tol", 1e-4)
         p.cg_max_iter = desc.get("cg_max_iter", 500)
+        p.pressure_solver = desc.get("pressure_solver", 0)
+        p.eos_stiffness = desc.get("eos_stiffness", 0.0)
+        p.eos_exponent = desc.get("eos_exponent", 7.0)
         self.params = p
         self.nf = len(desc["fluid_x"])
         self.nb = len(desc["boundary_x"])

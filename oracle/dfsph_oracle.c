@@ -16,6 +16,9 @@
  * own outputs; every reduction is a plain serial loop, so results do not depend on the
  * thread count.
  *
+ * Besides DFSPH the step implements the paper's EOS solver (WCSPH, Sec. 3.4.1) on the
+ * same density, non-pressure and pressure-acceleration building blocks.
+ *
  * Pins (see tests/test_oracle_*.py): kernel normalisation and gradient antisymmetry,
  * lattice rest density, brute-force neighbour sets, momentum antisymmetry of pressure,
  * viscosity and boundary forces, hydrostatic pressure in a resting tank, operator
@@ -387,6 +390,9 @@ typedef struct {
     float domain_min[3], domain_max[3];
     double xsph_c, cg_tol;
     int32_t cg_max_iter, pad_;
+    int32_t pressure_solver; /* 0 DFSPH, 1 WCSPH (equation of state, Sec. 3.4.1)           */
+    int32_t pad2_;
+    double eos_stiffness, eos_exponent;
 } or_params;
 
 typedef struct {
@@ -864,7 +870,7 @@ void or_step(or_ctx *c, double dt_in)
     for (int64_t i = 0; i < nf; ++i) c->kappa_v[i] = 0.0;
     int div_it = 0;
     double div_err = 0.0;
-    if (c->p.divergence_solve) {
+    if (c->p.divergence_solve && c->p.pressure_solver == 0) {
         double *kv = dalloc(nf);
         if (c->p.warm_start != 0) {
             /* warm start (DFSPH practice, a reading): half the previous step's total      */
@@ -909,7 +915,23 @@ void or_step(or_ctx *c, double dt_in)
     /* 6. warm start of the constant-density solve */
     double *k = dalloc(nf);
     for (int64_t i = 0; i < nf; ++i) { c->kappa[i] = 0.0; c->kappa0[i] = 0.0; }
-    if (c->p.warm_start != 0) {
+    int wcsph = c->p.pressure_solver == 1;
+    if (wcsph) {
+        /* WCSPH (Sec. 3.4.1 EOS solver inside Alg. general_algorithm): the pressure comes   */
+        /* from the current density by p = k ((rho/rho0)^gamma - 1), clamped at zero (a     */
+        /* reading: no tension at the free surface), and the pressure acceleration of Eq.    */
+        /* pressure_acceleration (plus the Akinci boundary term) is applied to v* once.  In  */
+        /* the stiffness form used by apply_kappa, kappa_i = p_i / rho_i (p/rho^2 =          */
+        /* kappa/rho).                                                                       */
+        for (int64_t i = 0; i < nf; ++i) {
+            double p = c->p.eos_stiffness * (pow(c->rho[i] / rho0, c->p.eos_exponent) - 1.0);
+            if (p < 0.0) p = 0.0;
+            k[i] = p / c->rho[i];
+            c->kappa[i] = k[i];
+        }
+        apply_kappa(c, k, dt);
+    }
+    if (c->p.warm_start != 0 && !wcsph) {
         /* gate: predicted density deviation with v* before any pressure of this step */
         double *dev = dalloc(nf);
         for (int64_t i = 0; i < nf; ++i) dev[i] = (c->rho[i] - rho0) + dt * drho_dt(c, i);
@@ -941,7 +963,7 @@ void or_step(or_ctx *c, double dt_in)
     /* 7. constant-density solve (Eq. density_source with rho* = rho - dt rho div v*) */
     int dens_it = 0;
     double dens_err = 0.0;
-    for (;;) {
+    for (; !wcsph;) {
         if (dens_it >= c->p.max_iter_density) break;
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < nf; ++i) {

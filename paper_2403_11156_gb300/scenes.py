@@ -22,6 +22,7 @@ import numpy as np
 
 VISC_NONE, VISC_EXPLICIT, VISC_XSPH, VISC_IMPLICIT = 0, 1, 2, 3
 WARM_ZERO, WARM_PREVIOUS, WARM_LEARNED = 0, 1, 2
+SOLVER_DFSPH, SOLVER_WCSPH = 0, 1
 
 
 def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, -9.81),
@@ -30,7 +31,8 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
            max_iter_density=100, min_iter_divergence=1, max_iter_divergence=100,
            viscosity_mode=VISC_EXPLICIT, warm_start=WARM_PREVIOUS, divergence_solve=1,
            xsph_c=0.0, cg_tol=1e-4, cg_max_iter=500, max_fluid_neighbors=0,
-           max_boundary_neighbors=0, cell_size=0.0, lanes_per_particle=0):
+           max_boundary_neighbors=0, cell_size=0.0, lanes_per_particle=0, pressure_solver=0,
+           eos_stiffness=0.0, eos_exponent=7.0):
     return dict(radius=float(radius), rest_density=float(rest_density),
                 viscosity=float(viscosity), gravity=tuple(float(g) for g in gravity),
                 domain_min=tuple(float(a) for a in domain_min),
@@ -45,7 +47,9 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
                 cg_tol=float(cg_tol), cg_max_iter=int(cg_max_iter),
                 max_fluid_neighbors=int(max_fluid_neighbors),
                 max_boundary_neighbors=int(max_boundary_neighbors),
-                cell_size=float(cell_size), lanes_per_particle=int(lanes_per_particle))
+                cell_size=float(cell_size), lanes_per_particle=int(lanes_per_particle),
+                pressure_solver=int(pressure_solver), eos_stiffness=float(eos_stiffness),
+                eos_exponent=float(eos_exponent))
 
 
 def lattice_block(n, spacing, origin, jitter=0.0, rng=None):
@@ -143,6 +147,25 @@ def dam_break_small(seed=1, n=(20, 20, 20), radius=0.01, box=0.8, jitter=1e-4, *
                     viscosity=0.01, dt_max=4e-4)
     defaults.update(kw)
     return _scene(fx, bx, params(**defaults))
+
+
+def wcsph_parameters(height, radius, rest_density=1000.0, gamma=7.0, mach=0.1, cfl=0.4):
+    """Equation-of-state parameters for a column of the given height (WCSPH practice; the
+    paper fixes none): a numerical sound speed c with the largest free-fall speed
+    sqrt(2 g height) at Mach `mach`, stiffness k = rho0 c^2 / gamma, and the acoustic step
+    dt = cfl h / c with h = 4r."""
+    c = np.sqrt(2.0 * 9.81 * height) / mach
+    return dict(pressure_solver=SOLVER_WCSPH, eos_stiffness=float(rest_density * c * c / gamma),
+                eos_exponent=float(gamma), dt_max=float(cfl * 4.0 * radius / c),
+                warm_start=WARM_ZERO, divergence_solve=0)
+
+
+def dam_break_wcsph(seed=1, n=(20, 20, 20), radius=0.01, box=0.8, **kw):
+    """The small dam break under the WCSPH pressure solver (Sec. 3.4.1), with the
+    equation-of-state parameters of wcsph_parameters for the column's height."""
+    p = wcsph_parameters(n[2] * 2.0 * radius, radius)
+    p.update(kw)
+    return dam_break_small(seed=seed, n=n, radius=radius, box=box, **p)
 
 
 def dam_break_rigid(seed=2, n=(125, 98, 98), radius=0.005, tank=(2.0, 1.0, 1.0),
