@@ -49,6 +49,13 @@ typedef enum sph_status {
 #define SPH_VISC_XSPH 2      /* XSPH velocity smoothing with coefficient xsph_c            */
 #define SPH_VISC_IMPLICIT 3  /* (I - dt A) v* = v~ of Sec. 3.6.2, matrix-free CG          */
 
+/* pressure_solver */
+#define SPH_SOLVER_DFSPH 0   /* divergence-free + constant-density Jacobi solves (Sec. 3.4.2) */
+#define SPH_SOLVER_WCSPH 1   /* equation of state p = k ((rho/rho0)^gamma - 1), clamped at 0, */
+                             /* applied once per step (Sec. 3.4.1, Alg. general_algorithm);  */
+                             /* warm_start, divergence_solve and the iteration limits are    */
+                             /* ignored                                                      */
+
 /* warm_start of the two DFSPH solves */
 #define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */
 #define SPH_WARM_PREVIOUS 1  /* half the previous step's kappa where the fluid compresses */
@@ -105,6 +112,9 @@ typedef struct sph_scene_desc {
                                   /* particles in the context, 2 up to twice that,    */
                                   /* else 1).  A batch uses the largest value given   */
                                   /* by its scenes.                                   */
+    int32_t pressure_solver;      /* SPH_SOLVER_*                                     */
+    float eos_stiffness;          /* WCSPH k, Pa (> 0)                                */
+    float eos_exponent;           /* WCSPH gamma (>= 1; 0 = 7)                        */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

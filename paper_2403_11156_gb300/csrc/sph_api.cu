@@ -51,7 +51,7 @@ struct sph_ctx {
     std::vector<int32_t> nbody_scene;
     int max_bodies = 0;
     bool any_moving = false, any_div = false, any_warm_div = false, any_warm = false,
-         any_learned = false, any_bodies = false, any_implicit = false;
+         any_learned = false, any_bodies = false, any_implicit = false, any_wcsph = false;
     Ptrs P{};
     SceneDev *d_scenes = nullptr;
 
@@ -164,6 +164,11 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
+    if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH) return bad("pressure_solver");
+    if (d.pressure_solver == SPH_SOLVER_WCSPH &&
+        (!(d.eos_stiffness > 0.0f) || !std::isfinite(d.eos_stiffness) || !(d.eos_exponent == 0.0f || d.eos_exponent >= 1.0f) ||
+         !std::isfinite(d.eos_exponent)))
+        return bad("eos_stiffness / eos_exponent");
     if (d.cell_size > 0.0f && !(d.cell_size >= half_cell(d.radius))) return bad("cell_size below h/2 (1 + 2^-8)");
     if (!std::isfinite(d.cell_size)) return bad("cell_size not finite");
     if (d.n_bodies < 0 || d.n_bodies > SPH_MAX_BODIES) return bad("n_bodies out of range");
@@ -462,8 +467,11 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     if (c->any_warm) {
         run(c, s, "warm_density", [&] { launch_warm_density(P, s); });
         if (c->any_learned) run(c, s, "mlp_warm", [&] { launch_mlp_warm(P, s); });
-        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, 0, 0, s); });
     }
+    // the warm-start pressure of the density solve, or the WCSPH equation-of-state pressure
+    // (written by the non-pressure kernel), applied once
+    if (c->any_warm || c->any_wcsph)
+        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, 0, 0, s); });
     if ((st = loop(1)) != SPH_OK) return st;
     if (c->any_bodies) {
         run(c, s, "body_force", [&] { launch_body_force(P, s); });
@@ -589,13 +597,18 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.dt_max = d.dt_max;
         q.cfl = d.cfl;
         q.two_r = 2.0f * d.radius;
-        q.min_it[0] = d.min_iter_divergence;
-        q.max_it[0] = d.max_iter_divergence;
-        q.min_it[1] = d.min_iter_density;
-        q.max_it[1] = d.max_iter_density;
+        const bool eos = d.pressure_solver == SPH_SOLVER_WCSPH;   // no iterative solves
+        q.min_it[0] = eos ? 0 : d.min_iter_divergence;
+        q.max_it[0] = eos ? 0 : d.max_iter_divergence;
+        q.min_it[1] = eos ? 0 : d.min_iter_density;
+        q.max_it[1] = eos ? 0 : d.max_iter_density;
         q.visc_mode = d.viscosity_mode;
-        q.warm = d.warm_start;
-        q.div_on = d.divergence_solve ? 1 : 0;
+        q.solver = d.pressure_solver;
+        const bool wc = d.pressure_solver == SPH_SOLVER_WCSPH;
+        q.eos_k = wc ? d.eos_stiffness : 0.0f;
+        q.eos_gamma = wc ? (d.eos_exponent > 0.0f ? d.eos_exponent : 7.0f) : 0.0f;
+        q.warm = wc ? 0 : d.warm_start;
+        q.div_on = (d.divergence_solve && !wc) ? 1 : 0;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;
         q.nbody = d.n_bodies;
@@ -634,10 +647,11 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         c->max_bodies = std::max(c->max_bodies, (int)d.n_bodies);
         c->any_moving |= d.n_bodies > 0;
         c->any_bodies |= d.n_bodies > 0;
-        c->any_div |= d.divergence_solve != 0;
-        c->any_warm_div |= d.divergence_solve != 0 && d.warm_start != 0;
-        c->any_warm |= d.warm_start != 0;
-        c->any_learned |= d.warm_start == 2;
+        c->any_div |= q.div_on != 0;
+        c->any_warm_div |= q.div_on != 0 && q.warm != 0;
+        c->any_warm |= q.warm != 0;
+        c->any_learned |= q.warm == 2;
+        c->any_wcsph |= q.solver == SPH_SOLVER_WCSPH;
         c->any_implicit |= d.viscosity_mode == 3;
     }
     if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * cap_f > 4.0e10)

@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
-    const bool run = WARM ? (sc.warm != 0 && (S == 1 || sc.div_on)) : (st.pending[S] != 0);  // uniform per block
+    // uniform per block; WCSPH scenes apply their equation-of-state pressure here
+    const bool run = WARM ? ((sc.warm != 0 && (S == 1 || sc.div_on)) || (S == 1 && sc.solver == 1))
+                          : (st.pending[S] != 0);
     if (run) {
         const int64_t i = c.i, NF = P.NF;
         const int s = c.s;
@@ -526,9 +528,19 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
     }
     v.w = rho_i;
     P.vel_c[i] = v;
-    P.ksum[i] = 0.0f;
+    // WCSPH: the equation of state of Sec. 3.4.1, p = k ((rho/rho0)^gamma - 1) clamped at
+    // zero, evaluated as k expm1(gamma log1p(rho/rho0 - 1)) for accuracy near rho0; the
+    // pressure pass then uses p/rho^2 (the kappa/rho slot) and the stiffness sum keeps
+    // p/rho (so that p = kappa_sum rho for output and for the rigid reaction)
+    float w = 0.0f, ks = 0.0f;
+    if (sc.solver == 1) {
+        const float p = fmaxf(sc.eos_k * expm1f(sc.eos_gamma * log1pf((rho_i - sc.rho0) / sc.rho0)), 0.0f);
+        ks = p / rho_i;
+        w = ks / rho_i;
+    }
+    P.ksum[i] = ks;
     P.k0[i] = 0.0f;
-    set_w(P.pos_s, i, 0.0f);
+    set_w(P.pos_s, i, w);
 }
 
 // Warm start of the constant-density solve: the predicted deviation rho* - rho0 with

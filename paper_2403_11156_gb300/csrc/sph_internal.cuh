@@ -50,6 +50,8 @@ struct SceneDev {
     float cg_tol;
     int32_t cg_max;
     float cull2;                      // (h + margin)^2: stencil cells farther are skipped
+    int32_t solver;                   // 0 DFSPH, 1 WCSPH
+    float eos_k, eos_gamma;           // WCSPH equation of state
 };
 
 // Per-scene mutable state (device).

@@ -75,7 +75,8 @@ class SceneDesc(C.Structure):
         ("viscosity_mode", C.c_int32), ("warm_start", C.c_int32),
         ("divergence_solve", C.c_int32), ("max_fluid_neighbors", C.c_int32),
         ("max_boundary_neighbors", C.c_int32), ("cg_tol", C.c_float), ("cg_max_iter", C.c_int32),
-        ("lanes_per_particle", C.c_int32),
+        ("lanes_per_particle", C.c_int32), ("pressure_solver", C.c_int32),
+        ("eos_stiffness", C.c_float), ("eos_exponent", C.c_float),
     ]
 
 
@@ -253,6 +254,9 @@ def _make_desc(d, keep):
     s.cg_tol = d.get("cg_tol", 1e-4)
     s.cg_max_iter = d.get("cg_max_iter", 500)
     s.lanes_per_particle = d.get("lanes_per_particle", 0)
+    s.pressure_solver = d.get("pressure_solver", 0)
+    s.eos_stiffness = d.get("eos_stiffness", 0.0)
+    s.eos_exponent = d.get("eos_exponent", 7.0)
     return s
 
 

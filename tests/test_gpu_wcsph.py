@@ -1,0 +1,107 @@
+"""GPU parity of the WCSPH pressure step (Sec. 3.4.1 equation of state inside Alg.
+general_algorithm, Eq. pressure_acceleration with the Akinci boundary term) against the
+oracle from identical states.
+
+Tolerances: density 1e-5 relative; pressure within 1e-5 gamma k (the change of
+k (rho/rho0)^gamma for a 1e-5 rho0 density error, the FP32 density's resolution) plus
+1e-5 relative; velocities within 1e-5 relative plus dt times the pressure acceleration
+that such a pressure error implies, which we bound by 1e-3 of the largest pressure
+velocity change (the pressures enter the acceleration summed over about 30 neighbours)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_11156_gb300 import scenes, sph
+
+from gpu_util import assert_rel, gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(**kw):
+    return scenes.dam_break_wcsph(seed=7, n=(9, 11, 13), box=0.4, **kw)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("visc", [0, 1])
+def test_one_step_fields(lanes, visc):
+    d = _small(lanes_per_particle=lanes, viscosity_mode=visc)
+    dt = d["dt_max"]
+    g = gpu_ctx(d)
+    o = oracle.Scene(d)
+    # a few steps build a compressed state; the last step starts from the GPU's state
+    for _ in range(5):
+        g.sph_step(dt)
+    x, v, _, _ = g.sph_read_state()
+    o.set_state(x, v, np.zeros(len(x), np.float32), np.zeros(len(x), np.float32))
+    g.sph_step(dt)
+    g.sph_synchronize(raise_on_error=False)
+    o.step(dt)
+    k, gamma = d["eos_stiffness"], d["eos_exponent"]
+    assert_rel(g.sph_read_field(sph.FIELD_RHO), o.get(oracle.RHO), 1e-5, what="rho")
+    x2, v2, rho2, p2 = g.sph_read_state()
+    p_ref = o.get(oracle.PRESSURE)
+    assert p_ref.max() > 0
+    assert np.abs(p2 - p_ref).max() <= 1e-5 * gamma * k + 1e-5 * np.abs(p_ref).max()
+    dv = o.get(oracle.V) - o.get(oracle.V_NONP)          # pressure velocity change
+    tol = 1e-3 * np.abs(dv).max() + 1e-5 * np.abs(o.get(oracle.V)).max()
+    assert np.abs(v2 - o.get(oracle.V)).max() <= tol
+    assert np.abs(x2 - o.get(oracle.X)).max() <= tol * dt + 1e-6
+    st = g.sph_get_stats()
+    assert st["dens_iters"] == 0 and st["div_iters"] == 0
+
+
+def test_rigid_coupling_parity():
+    # the rigid test scene under WCSPH, boxes in the fluid: the reaction on each body uses
+    # p/rho^2 in place of kappa/rho
+    d = scenes.dam_break_rigid(seed=9, n=(30, 22, 22), tank=(0.5, 0.25, 0.35), box_edge=0.04)
+    d.update(scenes.wcsph_parameters(22 * 2 * d["radius"], d["radius"]))
+    keep = np.ones(len(d["fluid_x"]), bool)
+    bx = d["boundary_x"].copy()
+    for kb, b in enumerate(d["bodies"]):
+        new = np.array([0.06 + 0.09 * kb, 0.125, 0.12])
+        sel = d["boundary_body"] == kb
+        bx[sel] += (new - np.array(b["com"])).astype(np.float32)
+        b["com"] = tuple(new)
+        keep &= ~np.all(np.abs(d["fluid_x"] - new) < 0.03, axis=1)
+    d["boundary_x"] = bx
+    d["fluid_x"], d["fluid_v"] = d["fluid_x"][keep], d["fluid_v"][keep]
+    dt = d["dt_max"]
+    g = gpu_ctx(d)
+    o = oracle.Scene(d)
+    g.sph_step(dt)
+    g.sph_synchronize(raise_on_error=False)
+    o.step(dt)
+    gb, ob = g.sph_read_bodies(), o.bodies()
+    assert np.abs(ob[:, 13:16]).max() > 0
+    for kb in range(len(gb)):
+        F, T = ob[kb, 13:16], ob[kb, 16:19]
+        np.testing.assert_allclose(gb[kb, 13:16], F, rtol=0, atol=2e-4 * np.abs(F).max() + 1e-9)
+        np.testing.assert_allclose(gb[kb, 16:19], T, rtol=0, atol=2e-4 * np.abs(T).max() + 1e-12)
+
+
+def test_dam_break_runs():
+    d = scenes.dam_break_wcsph()
+    g = gpu_ctx(d)
+    g.sph_steps(200, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    x, v, rho, p = g.sph_read_state()
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    assert rho.max() < 1.05 * d["rest_density"]
+    assert p.min() >= 0.0
+    st = g.sph_get_stats()
+    assert st["steps"] == 200 and st["flags"] == 0
+
+
+def test_mixed_batch_matches_single():
+    # a WCSPH scene and a DFSPH scene in one context step like their single contexts
+    ds = [_small(lanes_per_particle=1), scenes.dam_break_small(seed=4, n=(9, 11, 13), box=0.4,
+                                                               lanes_per_particle=1)]
+    dt = 2e-4
+    batch = gpu_ctx(ds)
+    batch.sph_steps(5, dt)
+    for k, d in enumerate(ds):
+        single = gpu_ctx(d)
+        single.sph_steps(5, dt)
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w)
