@@ -182,6 +182,31 @@ def batched_throughput(steps=30):
             "density_iters_range": [min(x["dens_iters"] for x in st), max(x["dens_iters"] for x in st)]}
 
 
+def wcsph_step_time(steps=50):
+    """The same 1.2M-particle dam break (without the boxes) under the WCSPH pressure solver
+    (Sec. 3.4.1), the algorithm of the paper's only timing table (Table 1, whose particle
+    count is not stated), at its acoustic step: milliseconds per step."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    d = scenes.dam_break_rigid(n_boxes=0)
+    d.update(scenes.wcsph_parameters(98 * 2 * d["radius"], d["radius"]))
+    nf = len(d["fluid_x"])
+    stream = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with sph.Context(d, stream=stream) as g:
+        g.sph_steps(5, 0.0)
+        g.sph_synchronize(raise_on_error=False)
+        a.record(stream)
+        g.sph_steps(steps, 0.0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        st = g.sph_get_stats()
+    return {"fluid_particles": nf, "dt": float(d["dt_max"]), "ms_per_step": ms,
+            "particle_steps_per_s": nf / (ms / 1000.0), "status_flags": int(st["flags"]),
+            "paper_table1_context": "Taichi CUDA WCSPH on A100: 0.0401 s/step, particle count not stated"}
+
+
 def reference_sample():
     from paper_2403_11156_gb300 import scenes
     # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
@@ -343,6 +368,9 @@ def main():
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_throughput()
+    wcsph = None
+    if rank == 0 and not args.no_batched:
+        wcsph = wcsph_step_time()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -365,6 +393,7 @@ def main():
         "clocks": clocks.summary(), "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
         "batched_64_scenes": batched,
+        "wcsph_1.2M": wcsph,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

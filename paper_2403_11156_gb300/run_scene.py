@@ -3,7 +3,8 @@
     python -m paper_2403_11156_gb300.run_scene --scene rigid --steps 2 --eager
 
 Workloads: small (8k-particle dam break), rigid (1.2M-particle dam break with rigid boxes),
-column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k particles).
+column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k particles),
+wcsph (the 8k dam break under the equation-of-state solver).
 --eager launches the kernels one by one (the form a kernel profiler can attribute);
 without it a step is one CUDA-graph launch.  --lanes sets the threads per particle of the
 neighbour sweeps (1, 2, 4; 0 chooses by size).
@@ -21,6 +22,7 @@ WORKLOADS = {
     "rigid": lambda: [scenes.dam_break_rigid()],
     "column": lambda: [scenes.viscous_column()],
     "batch": lambda: scenes.batch_dam_break(),
+    "wcsph": lambda: [scenes.dam_break_wcsph()],
 }
 
 
