@@ -102,6 +102,8 @@ def lib():
         L.or_get_bodies.argtypes = [C.c_void_p, dp]
         L.or_visc_operator.argtypes = [C.c_void_p, C.c_double, dp, dp]
         L.or_prepare.argtypes = [C.c_void_p]
+        L.or_pcisph_factor.argtypes = [C.c_void_p]
+        L.or_pcisph_factor.restype = C.c_double
         L.or_visc_solve.restype = C.c_int32
         L.or_visc_solve.argtypes = [C.c_void_p, C.c_double, dp, dp]
         L.or_mass.restype = C.c_double
@@ -310,6 +312,10 @@ class Scene:
         out = np.zeros_like(v)
         lib().or_visc_operator(self.ptr, float(dt), _p(v, C.c_double), _p(out, C.c_double))
         return out.reshape(-1, 3)
+
+    def pcisph_factor(self) -> float:
+        """PCISPH prototype stiffness delta dt^2 (Pa per kg/m^3 times s^2)."""
+        return float(lib().or_pcisph_factor(self.ptr))
 
     def prepare(self):
         """Neighbour lists, boundary pseudo-masses, density and alpha for the current

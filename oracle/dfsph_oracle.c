@@ -16,8 +16,9 @@
  * own outputs; every reduction is a plain serial loop, so results do not depend on the
  * thread count.
  *
- * Besides DFSPH the step implements the paper's EOS solver (WCSPH, Sec. 3.4.1) on the
- * same density, non-pressure and pressure-acceleration building blocks.
+ * Besides DFSPH the step implements the paper's EOS solver (WCSPH, Sec. 3.4.1) and
+ * PCISPH (an iterative PPE solver of Alg. ppe_solver) on the same density, non-pressure
+ * and pressure-acceleration building blocks.
  *
  * Pins (see tests/test_oracle_*.py): kernel normalisation and gradient antisymmetry,
  * lattice rest density, brute-force neighbour sets, momentum antisymmetry of pressure,
@@ -390,7 +391,7 @@ typedef struct {
     float domain_min[3], domain_max[3];
     double xsph_c, cg_tol;
     int32_t cg_max_iter, pad_;
-    int32_t pressure_solver; /* 0 DFSPH, 1 WCSPH (equation of state, Sec. 3.4.1)           */
+    int32_t pressure_solver; /* 0 DFSPH, 1 WCSPH (equation of state, Sec. 3.4.1), 2 PCISPH  */
     int32_t pad2_;
     double eos_stiffness, eos_exponent;
 } or_params;
@@ -857,6 +858,26 @@ int32_t or_visc_solve(or_ctx *c, double dt, const double *b, double *x)
     return (int32_t)c->stats[ST_CG_ITERS];
 }
 
+/* PCISPH stiffness of a prototype particle (the PCISPH reading of Alg. ppe_solver; the   */
+/* paper cites the method without restating it): with a full neighbourhood on the lattice */
+/* of spacing 2r, delta = 1 / (beta (|sum_j grad W_ij|^2 + sum_j |grad W_ij|^2)), beta =   */
+/* 2 (dt m / rho0)^2.  Returned without the 1/dt^2 factor.                                */
+double or_pcisph_factor(const or_ctx *c)
+{
+    double s = 2.0 * c->p.radius, gs[3] = {0, 0, 0}, g2 = 0.0;
+    int n = (int)ceil(c->h / s) + 1;
+    for (int a = -n; a <= n; ++a)
+        for (int b = -n; b <= n; ++b)
+            for (int e = -n; e <= n; ++e) {
+                double d[3] = {a * s, b * s, e * s}, g[3];
+                or_gradW(d, c->h, g);
+                for (int k = 0; k < 3; ++k) gs[k] += g[k];
+                g2 += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+            }
+    double mr = c->m / c->p.rest_density;
+    return 1.0 / (2.0 * mr * mr * (gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2] + g2));
+}
+
 void or_step(or_ctx *c, double dt_in)
 {
     double dt = dt_in > 0.0 ? dt_in : c->dt_next;
@@ -870,7 +891,7 @@ void or_step(or_ctx *c, double dt_in)
     for (int64_t i = 0; i < nf; ++i) c->kappa_v[i] = 0.0;
     int div_it = 0;
     double div_err = 0.0;
-    if (c->p.divergence_solve && c->p.pressure_solver == 0) {
+    if (c->p.divergence_solve && c->p.pressure_solver == 0) {   /* DFSPH only */
         double *kv = dalloc(nf);
         if (c->p.warm_start != 0) {
             /* warm start (DFSPH practice, a reading): half the previous step's total      */
@@ -915,7 +936,7 @@ void or_step(or_ctx *c, double dt_in)
     /* 6. warm start of the constant-density solve */
     double *k = dalloc(nf);
     for (int64_t i = 0; i < nf; ++i) { c->kappa[i] = 0.0; c->kappa0[i] = 0.0; }
-    int wcsph = c->p.pressure_solver == 1;
+    int wcsph = c->p.pressure_solver == 1, pcisph = c->p.pressure_solver == 2;
     if (wcsph) {
         /* WCSPH (Sec. 3.4.1 EOS solver inside Alg. general_algorithm): the pressure comes   */
         /* from the current density by p = k ((rho/rho0)^gamma - 1), clamped at zero (a     */
@@ -931,7 +952,7 @@ void or_step(or_ctx *c, double dt_in)
         }
         apply_kappa(c, k, dt);
     }
-    if (c->p.warm_start != 0 && !wcsph) {
+    if (c->p.warm_start != 0 && !wcsph && !pcisph) {
         /* gate: predicted density deviation with v* before any pressure of this step */
         double *dev = dalloc(nf);
         for (int64_t i = 0; i < nf; ++i) dev[i] = (c->rho[i] - rho0) + dt * drho_dt(c, i);
@@ -960,9 +981,15 @@ void or_step(or_ctx *c, double dt_in)
         apply_kappa(c, k, dt);
     }
 
-    /* 7. constant-density solve (Eq. density_source with rho* = rho - dt rho div v*) */
+    /* 7. constant-density solve (Eq. density_source with rho* = rho - dt rho div v*).       */
+    /* PCISPH refines the total pressure instead: p <- max(p + delta (rho* - rho0), 0) with  */
+    /* the prototype's delta, and the velocity moves by the pressure acceleration of the      */
+    /* change (Eq. pressure_acceleration is linear in p, so this equals v* plus the          */
+    /* acceleration of the total pressure).  Same error measure and iteration limits.        */
     int dens_it = 0;
     double dens_err = 0.0;
+    double *ptot = pcisph ? dalloc(nf) : NULL;
+    double delta = pcisph ? or_pcisph_factor(c) / (dt * dt) : 0.0;
     for (; !wcsph;) {
         if (dens_it >= c->p.max_iter_density) break;
 #pragma omp parallel for schedule(static)
@@ -974,15 +1001,29 @@ void or_step(or_ctx *c, double dt_in)
         for (int64_t i = 0; i < nf; ++i) s += c->e_dens[i];
         dens_err = nf > 0 ? s / (double)nf / rho0 : 0.0;
         if (dens_it == 0) c->stats[ST_DENS_ERR0] = dens_err;
-        for (int64_t i = 0; i < nf; ++i) {
-            k[i] = c->alpha[i] * c->e_dens[i] / (dt * dt);
-            c->kappa[i] += k[i];
+        if (pcisph) {
+            for (int64_t i = 0; i < nf; ++i) {
+                double dev = (c->rho[i] - rho0) + dt * drho_dt(c, i);
+                double pn = ptot[i] + delta * dev;
+                if (pn < 0.0) pn = 0.0;
+                k[i] = (pn - ptot[i]) / c->rho[i];     /* pressure change as stiffness p/rho */
+                ptot[i] = pn;
+                c->kappa[i] += k[i];
+            }
+        } else {
+            for (int64_t i = 0; i < nf; ++i) {
+                k[i] = c->alpha[i] * c->e_dens[i] / (dt * dt);
+                c->kappa[i] += k[i];
+            }
         }
         apply_kappa(c, k, dt);
         ++dens_it;
         if (!((dens_err > c->p.eta_density) || dens_it < c->p.min_iter_density)) break;
     }
+    if (pcisph) /* the total pressure itself (the increments' sum, without their rounding) */
+        for (int64_t i = 0; i < nf; ++i) c->kappa[i] = ptot[i] / c->rho[i];
     free(k);
+    free(ptot);
     c->stats[ST_DENS_ITERS] = dens_it;
     c->stats[ST_DENS_ERR] = dens_err;
 

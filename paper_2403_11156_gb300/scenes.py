@@ -22,7 +22,7 @@ import numpy as np
 
 VISC_NONE, VISC_EXPLICIT, VISC_XSPH, VISC_IMPLICIT = 0, 1, 2, 3
 WARM_ZERO, WARM_PREVIOUS, WARM_LEARNED = 0, 1, 2
-SOLVER_DFSPH, SOLVER_WCSPH = 0, 1
+SOLVER_DFSPH, SOLVER_WCSPH, SOLVER_PCISPH = 0, 1, 2
 
 
 def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, -9.81),
@@ -164,6 +164,15 @@ def dam_break_wcsph(seed=1, n=(20, 20, 20), radius=0.01, box=0.8, **kw):
     """The small dam break under the WCSPH pressure solver (Sec. 3.4.1), with the
     equation-of-state parameters of wcsph_parameters for the column's height."""
     p = wcsph_parameters(n[2] * 2.0 * radius, radius)
+    p.update(kw)
+    return dam_break_small(seed=seed, n=n, radius=radius, box=box, **p)
+
+
+def dam_break_pcisph(seed=1, n=(20, 20, 20), radius=0.01, box=0.8, **kw):
+    """The small dam break under PCISPH (pressure refined iteratively to the same 0.1 %
+    density tolerance; no divergence solve, no warm start)."""
+    p = dict(pressure_solver=SOLVER_PCISPH, warm_start=WARM_ZERO, divergence_solve=0,
+             min_iter_density=3)
     p.update(kw)
     return dam_break_small(seed=seed, n=n, radius=radius, box=box, **p)
 
