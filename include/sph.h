@@ -55,6 +55,11 @@ typedef enum sph_status {
                              /* applied once per step (Sec. 3.4.1, Alg. general_algorithm);  */
                              /* warm_start, divergence_solve and the iteration limits are    */
                              /* ignored                                                      */
+#define SPH_SOLVER_PCISPH 2  /* predictive-corrective PPE solve (Alg. ppe_solver): the total */
+                             /* pressure is refined by p <- max(p + delta (rho* - rho0), 0)   */
+                             /* with a prototype particle's delta until the density error     */
+                             /* meets eta_density (min/max_iter_density); no divergence       */
+                             /* solve, no warm start                                          */
 
 /* warm_start of the two DFSPH solves */
 #define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */

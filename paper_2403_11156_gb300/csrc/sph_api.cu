@@ -21,6 +21,31 @@ namespace {
 constexpr int kDefaultCapF = 96;
 constexpr int kDefaultCapB = 64;
 constexpr int64_t kAutoLaneThreads = 152 * 2048;  // resident threads of a full GB300
+
+// PCISPH stiffness of a prototype particle with a full neighbourhood on the lattice of
+// spacing 2r (the predictive-corrective solver's constant): delta dt^2 = 1 / (2 (m/rho0)^2
+// (|sum grad W|^2 + sum |grad W|^2)), the cubic spline's gradient dW/dr = 48/(pi h^4) g(q),
+// g = q (3q - 2) for q <= 1/2 and -(1 - q)^2 up to q = 1.
+double pcisph_prototype(double r)
+{
+    const double h = 4.0 * r, s = 2.0 * r, pi = 3.14159265358979323846;
+    const int n = (int)std::ceil(h / s) + 1;
+    double sum[3] = {0.0, 0.0, 0.0}, sq = 0.0;
+    for (int a = -n; a <= n; ++a)
+        for (int b = -n; b <= n; ++b)
+            for (int e = -n; e <= n; ++e) {
+                const double x[3] = {a * s, b * s, e * s};
+                const double d = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                const double q = d / h;
+                if (!(d > 0.0) || q > 1.0) continue;
+                const double g = q <= 0.5 ? q * (3.0 * q - 2.0) : -(1.0 - q) * (1.0 - q);
+                const double f = 48.0 / (pi * h * h * h * h) * g / d;
+                for (int k = 0; k < 3; ++k) sum[k] += f * x[k];
+                sq += f * f * d * d;
+            }
+    const double mr = s * s * s;   // m / rho0
+    return 1.0 / (2.0 * mr * mr * (sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2] + sq));
+}
 constexpr double kPi = 3.14159265358979323846;
 
 struct Alloc {
@@ -164,7 +189,9 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
-    if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH) return bad("pressure_solver");
+    if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH &&
+        d.pressure_solver != SPH_SOLVER_PCISPH)
+        return bad("pressure_solver");
     if (d.pressure_solver == SPH_SOLVER_WCSPH &&
         (!(d.eos_stiffness > 0.0f) || !std::isfinite(d.eos_stiffness) || !(d.eos_exponent == 0.0f || d.eos_exponent >= 1.0f) ||
          !std::isfinite(d.eos_exponent)))
@@ -598,8 +625,9 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.cfl = d.cfl;
         q.two_r = 2.0f * d.radius;
         const bool eos = d.pressure_solver == SPH_SOLVER_WCSPH;   // no iterative solves
-        q.min_it[0] = eos ? 0 : d.min_iter_divergence;
-        q.max_it[0] = eos ? 0 : d.max_iter_divergence;
+        const bool no_div = eos || d.pressure_solver == SPH_SOLVER_PCISPH;
+        q.min_it[0] = no_div ? 0 : d.min_iter_divergence;
+        q.max_it[0] = no_div ? 0 : d.max_iter_divergence;
         q.min_it[1] = eos ? 0 : d.min_iter_density;
         q.max_it[1] = eos ? 0 : d.max_iter_density;
         q.visc_mode = d.viscosity_mode;
@@ -607,8 +635,10 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         const bool wc = d.pressure_solver == SPH_SOLVER_WCSPH;
         q.eos_k = wc ? d.eos_stiffness : 0.0f;
         q.eos_gamma = wc ? (d.eos_exponent > 0.0f ? d.eos_exponent : 7.0f) : 0.0f;
-        q.warm = wc ? 0 : d.warm_start;
-        q.div_on = (d.divergence_solve && !wc) ? 1 : 0;
+        const bool pci = d.pressure_solver == SPH_SOLVER_PCISPH;
+        q.warm = (wc || pci) ? 0 : d.warm_start;
+        q.div_on = (d.divergence_solve && !wc && !pci) ? 1 : 0;
+        q.pci_c = pci ? (float)pcisph_prototype(d.radius) : 0.0f;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;
         q.nbody = d.n_bodies;

@@ -348,6 +348,15 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
             ei = fmaxf(D, 0.0f);
             kappa = P.alpha[i] * ei / dt;
             P.kvsum[i] += kappa;
+        } else if (sc.solver == 2) {
+            // PCISPH: refine the total pressure p <- max(p + delta (rho* - rho0), 0) with
+            // the prototype's delta; the pass B applies the change (kept as p/rho)
+            const float dev = fmaf(dt, D, rho - sc.rho0);
+            ei = fmaxf(dev, 0.0f);
+            const float p_old = P.ksum[i] * rho;
+            const float p_new = fmaxf(fmaf(sc.pci_c / (dt * dt), dev, p_old), 0.0f);
+            kappa = (p_new - p_old) / rho;
+            P.ksum[i] = p_new / rho;
         } else {
             ei = fmaxf(fmaf(dt, D, rho - sc.rho0), 0.0f);
             kappa = P.alpha[i] * ei / (dt * dt);

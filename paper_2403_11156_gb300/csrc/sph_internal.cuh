@@ -50,8 +50,9 @@ struct SceneDev {
     float cg_tol;
     int32_t cg_max;
     float cull2;                      // (h + margin)^2: stencil cells farther are skipped
-    int32_t solver;                   // 0 DFSPH, 1 WCSPH
+    int32_t solver;                   // 0 DFSPH, 1 WCSPH, 2 PCISPH
     float eos_k, eos_gamma;           // WCSPH equation of state
+    float pci_c;                      // PCISPH prototype stiffness times dt^2
 };
 
 // Per-scene mutable state (device).
