@@ -207,6 +207,35 @@ def wcsph_step_time(steps=50):
             "paper_table1_context": "Taichi CUDA WCSPH on A100: 0.0401 s/step, particle count not stated"}
 
 
+def solver_comparison(seconds=0.04):
+    """The 8,000-particle dam break under the three pressure solvers the paper implements,
+    each at its own step (DFSPH and PCISPH 4e-4 s at the 0.1 % density tolerance, WCSPH its
+    acoustic step), over the same simulated time: iterations per step and GPU milliseconds
+    per simulated second."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    out = {}
+    for name, d in (("dfsph", scenes.dam_break_small()), ("pcisph", scenes.dam_break_pcisph()),
+                    ("wcsph", scenes.dam_break_wcsph())):
+        dt = float(d["dt_max"])
+        steps = max(1, int(round(seconds / dt)))
+        stream = torch.cuda.Stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with sph.Context(d, stream=stream) as g:
+            a.record(stream)
+            g.sph_steps(steps, dt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            st = g.sph_get_stats()
+        out[name] = {"dt": dt, "steps": steps, "ms_per_step": ms / steps,
+                     "ms_per_simulated_second": ms / (steps * dt),
+                     "density_iters_per_step": st["total_dens_iters"] / steps,
+                     "divergence_iters_per_step": st["total_div_iters"] / steps,
+                     "final_density_error": st["dens_err"]}
+    return out
+
+
 def reference_sample():
     from paper_2403_11156_gb300 import scenes
     # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
@@ -369,8 +398,10 @@ def main():
     if rank == 0 and not args.no_batched:
         batched = batched_throughput()
     wcsph = None
+    solvers = None
     if rank == 0 and not args.no_batched:
         wcsph = wcsph_step_time()
+        solvers = solver_comparison()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -394,6 +425,7 @@ def main():
         "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
         "batched_64_scenes": batched,
         "wcsph_1.2M": wcsph,
+        "solvers_8k": solvers,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
