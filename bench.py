@@ -146,25 +146,40 @@ def learned_vs_plain():
     return out
 
 
-def batched_throughput(steps=30):
+def batched_throughput(steps=30, rank=0, world=1, barrier=lambda: None):
     """64 independent dam breaks (20k-200k particles, log-uniform, seed 5) in one context:
-    every kernel of a step covers all scenes in one launch.  Returns particle-steps/s of
-    the batch and of the same scenes stepped one at a time (8 of them, scaled)."""
+    every kernel of a step covers all scenes in one launch.  With several GPUs each rank
+    steps its share of the scenes (largest first onto the least-loaded rank) and the
+    whole-job rate is the sum of particles over the slowest rank's time.  Returns
+    particle-steps/s of the batch and, on one GPU, of the same scenes stepped one at a
+    time (8 of them, scaled)."""
     import torch
     from paper_2403_11156_gb300 import scenes, sph
-    ds = scenes.batch_dam_break()
+    from paper_2403_11156_gb300.sharding import reduce_timing, shard_scenes
+    ds_all = scenes.batch_dam_break()
+    mine = shard_scenes([len(d["fluid_x"]) for d in ds_all], world)[rank]
+    ds = [ds_all[k] for k in mine]
     nf = sum(len(d["fluid_x"]) for d in ds)
     stream = torch.cuda.Stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with sph.Context(ds, stream=stream) as g:
         g.sph_steps(5, 0.0)
         g.sph_synchronize(raise_on_error=False)
+        barrier()
+        torch.cuda.synchronize()
         a.record(stream)
         g.sph_steps(steps, 0.0)
         b.record(stream)
         torch.cuda.synchronize()
+        barrier()
         ms = a.elapsed_time(b) / steps
         st = [g.sph_get_stats(k) for k in range(len(ds))]
+    ms, nf_all = reduce_timing(ms, nf, world, device="cuda")
+    out = {"scenes": len(ds_all), "fluid_particles": int(nf_all), "ranks": world, "ms_per_step": ms,
+           "particle_steps_per_s": nf_all / (ms / 1000.0),
+           "density_iters_range": [min(x["dens_iters"] for x in st), max(x["dens_iters"] for x in st)]}
+    if world > 1:
+        return out
     single_ms, single_n = 0.0, 0
     for k in range(0, len(ds), 8):
         with sph.Context(ds[k], stream=stream) as g:
@@ -176,10 +191,8 @@ def batched_throughput(steps=30):
             torch.cuda.synchronize()
             single_ms += a.elapsed_time(b) / steps
             single_n += len(ds[k]["fluid_x"])
-    return {"scenes": len(ds), "fluid_particles": nf, "ms_per_step": ms,
-            "particle_steps_per_s": nf / (ms / 1000.0),
-            "one_at_a_time_particle_steps_per_s": single_n / (single_ms / 1000.0),
-            "density_iters_range": [min(x["dens_iters"] for x in st), max(x["dens_iters"] for x in st)]}
+    out["one_at_a_time_particle_steps_per_s"] = single_n / (single_ms / 1000.0)
+    return out
 
 
 def wcsph_step_time(steps=50):
@@ -297,6 +310,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2403_11156_gb300 import build, scenes, sph
+    from paper_2403_11156_gb300.sharding import reduce_timing
 
     build.build()
     torch.cuda.set_device(local)
@@ -333,11 +347,8 @@ def main():
     status = g.sph_synchronize(raise_on_error=False)
     it1 = g.sph_get_stats()
     launches = g.sph_launch_count() - l0
-    t_max = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = world * n_fluid * args.steps / (ms / 1000.0)
+    ms, units = reduce_timing(ms, n_fluid * args.steps, world, device="cuda")
+    value = units / (ms / 1000.0)
 
     # ---- end to end through the C ABI: each step enqueued with a host dt and its
     # positions read back into pinned host memory
@@ -353,8 +364,9 @@ def main():
         with torch.cuda.stream(stream):
             pinned.copy_(dev_x, non_blocking=True)
         stream.synchronize()
-    e2e_s = time.perf_counter() - t
-    e2e = {"value": world * n_fluid * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4,
+    e2e_ms, e2e_units = reduce_timing((time.perf_counter() - t) * 1000.0, n_fluid * e2e_steps, world,
+                                      device="cuda")
+    e2e = {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 4,
            "d2h_bytes_per_step": 12 * n_fluid}
 
     # ---- kernel breakdown: eager steps with CUDA events around every launch
@@ -395,8 +407,8 @@ def main():
     if rank == 0 and not args.no_learned:
         learned = learned_vs_plain()
     batched = None
-    if rank == 0 and not args.no_batched:
-        batched = batched_throughput()
+    if not args.no_batched:
+        batched = batched_throughput(rank=rank, world=world, barrier=barrier)
     wcsph = None
     solvers = None
     if rank == 0 and not args.no_batched:
