@@ -985,6 +985,20 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
                     best.lanes = lanes_c[b];
                 }
             }
+        // keep the default configuration (27-cell stencil, gather batch 4, lanes by size)
+        // unless a candidate is more than 3 % faster: short trials are noisy, and the
+        // default is the one whose kernels are profiled
+        int64_t nf_all = 0;
+        for (int s = 0; s < n; ++s) nf_all += descs[s].n_fluid;
+        const int def_lanes = fixed_lanes ? fixed_lanes
+                                          : (nf_all * 4 <= kAutoLaneThreads ? 4 : (nf_all * 2 <= kAutoLaneThreads ? 2 : 1));
+        for (int k = 0; k < best.n_trials; ++k)
+            if (best.trial_cell_factor[k] == factors[0] && best.trial_batch[k] == 4 &&
+                best.trial_lanes[k] == def_lanes && best.trial_ms[k] <= 1.03f * best_ms) {
+                best.cell_factor = factors[0];
+                best.gather_batch = 4;
+                best.lanes = def_lanes;
+            }
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
     }

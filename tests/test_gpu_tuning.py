@@ -2,8 +2,9 @@
 (key, id) order and the neighbour counts stay bit-exact against the oracle's contracts
 (the oracle's key function takes the cell size as a parameter), density and alpha stay
 within 1e-5; autotuning times eight candidates (two cell sizes times (threads per
-particle, gather batch) in (1, 4), (1, 8), (2, 4), (4, 4)), keeps the fastest and caches
-it; lanes_per_particle given by the caller stays fixed."""
+particle, gather batch) in (1, 4), (1, 8), (2, 4), (4, 4)), keeps the fastest (or the
+default configuration when it is within 3 % of the fastest) and caches it;
+lanes_per_particle given by the caller stays fixed."""
 import numpy as np
 import pytest
 
@@ -43,8 +44,12 @@ def test_autotune_picks_fastest_and_caches():
     assert t["tuned"] == 1 and t["from_cache"] == 0 and len(t["trials"]) == 8
     assert sorted({(r["lanes"], r["gather_batch"]) for r in t["trials"]}) == [(1, 4), (1, 8), (2, 4), (4, 4)]
     best = min(t["trials"], key=lambda r: r["ms_per_step"])
-    assert t["gather_batch"] == best["gather_batch"] and t["cell_factor"] == pytest.approx(best["cell_factor"])
-    assert t["lanes"] == best["lanes"]
+    chosen = [r for r in t["trials"] if (r["lanes"], r["gather_batch"]) == (t["lanes"], t["gather_batch"])
+              and r["cell_factor"] == pytest.approx(t["cell_factor"])]
+    assert len(chosen) == 1
+    # the fastest, or the default configuration within 3 % of it
+    default = (t["cell_factor"] == pytest.approx(1.00390625) and t["gather_batch"] == 4)
+    assert chosen[0] is best or (default and chosen[0]["ms_per_step"] <= 1.03 * best["ms_per_step"])
     g.sph_steps(20, 0.0)
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
     st = g.sph_get_stats()
