@@ -11,8 +11,9 @@ shares nothing with the CUDA library:
   into the six tetrahedra around its main diagonal; per tetrahedron the corners above the
   iso-level (in float32, as the field is float32) are cut off by one triangle (one or
   three corners above) or a quad split into two triangles (two above), vertices linearly
-  interpolated along the cut edges, triangles oriented with the normal pointing from the
-  corners above to the corners below (outward for a fluid).
+  interpolated along the cut edges from the corner above to the corner below, triangles
+  oriented with the normal pointing from the corners above to the corners below (outward
+  for a fluid).
 * height_map: a headless orthographic view down the -z axis of the particles as spheres
   of radius R: per pixel centre (u, v), the largest z + sqrt(R^2 - d^2) over particles
   whose disk covers it (d < R), else no hit.
@@ -87,10 +88,12 @@ def marching_tetrahedra(field, origin, spacing, iso) -> np.ndarray:
                     outs = [c for c in tet if not ab[c]]
                     if len(ins) in (0, 4):
                         continue
-                    if len(ins) == 1 or len(ins) == 3:
-                        a = ins[0] if len(ins) == 1 else outs[0]
-                        others = outs if len(ins) == 1 else ins
-                        tris = [[_cut(pos[a], pos[b], val[a], val[b], iso) for b in others]]
+                    if len(ins) == 1:
+                        a = ins[0]
+                        tris = [[_cut(pos[a], pos[b], val[a], val[b], iso) for b in outs]]
+                    elif len(ins) == 3:
+                        b = outs[0]
+                        tris = [[_cut(pos[a], pos[b], val[a], val[b], iso) for a in ins]]
                     else:
                         a0, a1 = ins
                         b0, b1 = outs
