@@ -344,6 +344,39 @@ sph_status sph_grid_order_noalloc(const float *x, int64_t n, const float *domain
                                   const float *domain_max, float cell_size, int32_t *order,
                                   uint32_t *keys, void *stream);
 
+/* Post-processing (Sec. 4.3: surface reconstruction of the fluid particles, then rendering;
+ * the paper uses SplashSurf and Blender, these are CUDA kernels writing device buffers).
+ *
+ * sph_surface_field: the fluid's volume fraction phi(g) = sum_j (m / rho_j) W(|g - x_j|)
+ * (the SPH interpolant of Sec. 3.2 applied to 1: about 1 inside, 0 outside) at the grid
+ * nodes origin + spacing (i, j, k), 0 <= i < dims[0] ..., for scene `scene` at its
+ * current positions, rho_j the density of the last step (rho0 before the first step).
+ * field: device float [dims[2]][dims[1]][dims[0]].  Enqueued on the context's stream;
+ * returns after enqueueing.  The reconstruction of a surface is the iso-level 0.5 of
+ * this field (sph_surface_mesh). */
+sph_status sph_surface_field(sph_ctx *ctx, int32_t scene, const float origin[3], float spacing,
+                             const int32_t dims[3], float *field);
+
+/* Iso-surface phi = iso of a device grid field laid out as above, by marching tetrahedra:
+ * each grid cube is split into the six tetrahedra around its diagonal from node (i, j, k)
+ * to (i+1, j+1, k+1); per tetrahedron the corners with phi > iso are cut off by one or
+ * two triangles whose vertices interpolate linearly along the cut edges, oriented with
+ * the normal pointing from phi > iso towards phi <= iso (outward for a fluid).  tris:
+ * device float [cap][3][3], triangles in cube order (x fastest); *n_tris (host) receives
+ * the total, which may exceed cap (then only cap triangles are written and SPH_EOVERFLOW
+ * is returned).  Enqueued on stream, which the call synchronises. */
+sph_status sph_surface_mesh(const float *field, const int32_t dims[3], const float origin[3],
+                            float spacing, float iso, float *tris, int64_t cap, int64_t *n_tris,
+                            void *stream);
+
+/* Headless orthographic height map of scene `scene` viewed down the -z axis: pixel (i, j)
+ * (centre lo + ((i + 0.5)(hi - lo)_x / width, (j + 0.5)(hi - lo)_y / height)) receives the
+ * largest z + sqrt(radius^2 - d^2) over particles whose disk of the given radius covers
+ * it (d < radius), NaN where none does.  out: device float [height][width].  Enqueued on
+ * the context's stream; returns after enqueueing. */
+sph_status sph_render_heightmap(sph_ctx *ctx, int32_t scene, const float lo[2], const float hi[2],
+                                int32_t width, int32_t height, float radius, float *out);
+
 const char *sph_status_string(sph_status s);
 
 /* Message of the last failing call on ctx (never NULL). */

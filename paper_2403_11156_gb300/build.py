@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 
-SOURCES = ["sph_grid.cu", "sph_fluid.cu", "sph_rigid.cu", "sph_visc.cu", "sph_mlp.cu", "sph_mlp_train.cu", "sph_api.cu", "sph_noalloc.cu"]
+SOURCES = ["sph_grid.cu", "sph_fluid.cu", "sph_rigid.cu", "sph_visc.cu", "sph_mlp.cu", "sph_mlp_train.cu", "sph_api.cu", "sph_noalloc.cu", "sph_post.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

@@ -1054,6 +1054,43 @@ sph_status sph_create_batch(const sph_scene_desc *scenes, int32_t n, const sph_a
     return create_impl(scenes, n, alloc, stream, out);
 }
 
+sph_status sph_surface_field(sph_ctx *c, int32_t scene, const float origin[3], float spacing, const int32_t dims[3],
+                             float *field)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (scene < 0 || scene >= c->nscenes) return fail(c, SPH_EINVAL, "scene %d out of range", scene);
+    if (!origin || !dims || !field || !(spacing > 0.0f) || !std::isfinite(spacing))
+        return fail(c, SPH_EINVAL, "surface field: bad grid");
+    int64_t nodes = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || !std::isfinite(origin[a])) return fail(c, SPH_EINVAL, "surface field: bad grid");
+        nodes *= dims[a];
+    }
+    if (nodes > ((int64_t)1 << 31)) return fail(c, SPH_EINVAL, "surface field: grid too large");
+    const SceneDev &q = c->scenes[scene];
+    cudaError_t e = post_surface_field(q, c->P.pos_c + q.f_off, c->P.vel_c + q.f_off, origin, spacing, dims, field,
+                                       c->stream);
+    if (e != cudaSuccess) return fail(c, SPH_ECUDA, "surface field: %s", cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+sph_status sph_render_heightmap(sph_ctx *c, int32_t scene, const float lo[2], const float hi[2], int32_t width,
+                                int32_t height, float radius, float *out)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (scene < 0 || scene >= c->nscenes) return fail(c, SPH_EINVAL, "scene %d out of range", scene);
+    if (!lo || !hi || !out || width < 1 || height < 1 || (int64_t)width * height > ((int64_t)1 << 31) ||
+        !(radius > 0.0f) || !std::isfinite(radius) || !(hi[0] > lo[0]) || !(hi[1] > lo[1]) ||
+        !std::isfinite(lo[0]) || !std::isfinite(lo[1]) || !std::isfinite(hi[0]) || !std::isfinite(hi[1]))
+        return fail(c, SPH_EINVAL, "height map: bad view");
+    const SceneDev &q = c->scenes[scene];
+    cudaError_t e = post_height_map(c->P.pos_c + q.f_off, q.nf, lo, hi, width, height, radius, out, c->stream);
+    if (e != cudaSuccess) return fail(c, SPH_ECUDA, "height map: %s", cudaGetErrorString(e));
+    return SPH_OK;
+}
+
 sph_status sph_get_tuning(sph_ctx *c, sph_tuning *out)
 {
     sph_status st = check_ctx(c);

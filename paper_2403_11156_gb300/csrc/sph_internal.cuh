@@ -248,6 +248,12 @@ void launch_cg_ap(const Ptrs &P, cudaStream_t s);
 void launch_cg_xr(const Ptrs &P, cudaStream_t s);
 void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
 
+// ------------------------------------------------------------------ post-processing (sph_post.cu)
+cudaError_t post_surface_field(const SceneDev &sc, const float4 *pos, const float4 *vel, const float origin[3],
+                               float spacing, const int32_t dims[3], float *out, cudaStream_t s);
+cudaError_t post_height_map(const float4 *pos, int64_t n, const float lo[2], const float hi[2], int32_t w,
+                            int32_t h, float radius, float *out, cudaStream_t s);
+
 // ------------------------------------------------------------------ rigid (sph_rigid.cu)
 void launch_boundary_update(const Ptrs &P, cudaStream_t s);
 void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);

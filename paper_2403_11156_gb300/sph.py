@@ -161,11 +161,15 @@ def load():
     L.sph_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     L.sph_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.sph_mlp_train.argtypes = [vp, vp, C.c_int64, vp, vp, ip, ip, C.c_float, C.c_uint64, vp, vp, vp]
+    L.sph_surface_field.argtypes = [vp, ip, fp, C.c_float, C.POINTER(C.c_int32), vp]
+    L.sph_surface_mesh.argtypes = [vp, C.POINTER(C.c_int32), fp, C.c_float, C.c_float, vp, C.c_int64,
+                                   C.POINTER(C.c_int64), vp]
+    L.sph_render_heightmap.argtypes = [vp, ip, fp, fp, ip, ip, C.c_float, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
                  "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
-                 "sph_read_trace"):
+                 "sph_read_trace", "sph_surface_field", "sph_surface_mesh", "sph_render_heightmap"):
         getattr(L, name).restype = C.c_int32
     _lib = L
     return L
@@ -408,6 +412,27 @@ class Context:
         _check(self.ctx, load().sph_launch_count(self.ctx, C.byref(n)))
         return n.value
 
+    def sph_surface_field(self, origin, spacing, dims, scene=0, out=None):
+        """Volume-fraction field on the grid (device tensor [dims[2]][dims[1]][dims[0]])."""
+        import torch
+        dims = [int(d) for d in dims]
+        if out is None:
+            out = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
+        o = (C.c_float * 3)(*origin)
+        d = (C.c_int32 * 3)(*dims)
+        _check(self.ctx, load().sph_surface_field(self.ctx, scene, o, float(spacing), d, out.data_ptr()))
+        return out
+
+    def sph_render_heightmap(self, lo, hi, width, height, radius, scene=0, out=None):
+        """Height map viewed down -z (device tensor [height][width], NaN where empty)."""
+        import torch
+        if out is None:
+            out = torch.empty((int(height), int(width)), dtype=torch.float32, device="cuda")
+        a, b = (C.c_float * 2)(*lo), (C.c_float * 2)(*hi)
+        _check(self.ctx, load().sph_render_heightmap(self.ctx, scene, a, b, int(width), int(height),
+                                                     float(radius), out.data_ptr()))
+        return out
+
 
 NOALLOC_MAX_POINTS = 262144
 NOALLOC_MAX_CELLS = 1048576
@@ -423,6 +448,30 @@ def sph_grid_order_noalloc(x, n, domain_min, domain_max, cell_size, order, keys=
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     return load().sph_grid_order_noalloc(ptr(x), int(n), lo, hi, float(cell_size), ptr(order),
                                          ptr(keys), st)
+
+
+def sph_surface_mesh(field, origin, spacing, iso=0.5, cap=None, stream=None):
+    """Marshal sph_surface_mesh on a device field tensor [nz][ny][nx]: returns the device
+    tensor of triangles [n][3][3] (grown and rerun once if the first capacity is short)."""
+    import torch
+    nz, ny, nx = (int(d) for d in field.shape)
+    dims = (C.c_int32 * 3)(nx, ny, nz)
+    o = (C.c_float * 3)(*origin)
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    if st is None:
+        st = torch.cuda.current_stream().cuda_stream
+    cap = int(cap) if cap is not None else max(1024, 4 * nx * ny)
+    for _ in range(2):
+        tris = torch.empty((cap, 3, 3), dtype=torch.float32, device=field.device)
+        n = C.c_int64()
+        status = load().sph_surface_mesh(field.data_ptr(), dims, o, float(spacing), float(iso),
+                                          tris.data_ptr(), cap, C.byref(n), st)
+        if status == SPH_EOVERFLOW:
+            cap = int(n.value)
+            continue
+        _check(None, status)
+        return tris[:n.value]
+    raise SphError(SPH_EOVERFLOW, "triangle count changed between runs")
 
 
 MLP_PARAMS = 4555
