@@ -249,6 +249,33 @@ def solver_comparison(seconds=0.04):
     return out
 
 
+def post_processing(g, desc, stream):
+    """Phase three (Sec. 4.3) on the benchmark scene's final state: the volume-fraction
+    field on a grid of spacing r over the tank, its 0.5 iso-surface, and a height map at
+    r/2 pixels; milliseconds of each (CUDA events)."""
+    import torch
+    from paper_2403_11156_gb300 import sph
+    r = desc["radius"]
+    lo, hi = desc["domain_min"], desc["domain_max"]
+    dims = [int((hi[a] - lo[a]) / r) + 1 for a in range(3)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        field = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
+        w, h = int((hi[0] - lo[0]) / (r / 2)), int((hi[1] - lo[1]) / (r / 2))
+        img = torch.empty((h, w), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        g.sph_surface_field(lo, r, dims, out=field)
+        ev[1].record(stream)
+        tris = sph.sph_surface_mesh(field, lo, r, 0.5, stream=stream)
+        ev[2].record(stream)
+        g.sph_render_heightmap(lo[:2], (lo[0] + w * r / 2, lo[1] + h * r / 2), w, h, r, out=img)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+    return {"grid": dims, "field_ms": ev[0].elapsed_time(ev[1]), "mesh_ms": ev[1].elapsed_time(ev[2]),
+            "triangles": int(len(tris)), "height_map": [w, h], "height_map_ms": ev[2].elapsed_time(ev[3])}
+
+
 def reference_sample():
     from paper_2403_11156_gb300 import scenes
     # the same construction scaled to 80 x 64 x 64 = 327,680 particles (tank 0.64x), so that
@@ -403,6 +430,9 @@ def main():
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4)}
                  for k, v in sorted(kt.items(), key=lambda t: -t[1][1])}
 
+    post = None
+    if rank == 0 and not args.no_batched:
+        post = post_processing(g, desc, stream)
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_vs_plain()
@@ -438,6 +468,7 @@ def main():
         "batched_64_scenes": batched,
         "wcsph_1.2M": wcsph,
         "solvers_8k": solvers,
+        "post_processing_1.2M": post,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -7,7 +7,9 @@ column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k p
 wcsph (the 8k dam break under the equation-of-state solver).
 --eager launches the kernels one by one (the form a kernel profiler can attribute);
 without it a step is one CUDA-graph launch.  --lanes sets the threads per particle of the
-neighbour sweeps (1, 2, 4; 0 chooses by size).
+neighbour sweeps (1, 2, 4; 0 chooses by size).  --surface / --image write the post-processing
+results of scene 0 after the steps: the iso-surface of the fluid (OBJ) and a shaded
+height map seen from above (PGM).
 """
 from __future__ import annotations
 
@@ -33,6 +35,9 @@ def main():
     ap.add_argument("--eager", action="store_true")
     ap.add_argument("--dt", type=float, default=0.0)
     ap.add_argument("--lanes", type=int, default=0, help="threads per particle (0: by size)")
+    ap.add_argument("--surface", default=None, help="write the fluid's iso-surface (OBJ) of scene 0 here")
+    ap.add_argument("--image", default=None, help="write a height-map image (PGM) of scene 0 here")
+    ap.add_argument("--grid", type=float, default=0.0, help="surface grid spacing (default: r)")
     args = ap.parse_args()
     build.build()
     descs = WORKLOADS[args.scene]()
@@ -47,6 +52,25 @@ def main():
     out = {"scene": args.scene, "scenes": len(descs), "steps": args.steps,
            "fluid_particles": int(sum(len(d["fluid_x"]) for d in descs)),
            "seconds": el, "status": sph.STATUS_NAMES[status], "stats": g.sph_get_stats(0)}
+    d0 = descs[0]
+    if args.surface:
+        # post-processing (Sec. 4.3): the volume-fraction field's 0.5 iso-surface
+        from paper_2403_11156_gb300 import export
+        s = args.grid or d0["radius"]
+        lo, hi = d0["domain_min"], d0["domain_max"]
+        dims = [int((hi[a] - lo[a]) / s) + 1 for a in range(3)]
+        field = g.sph_surface_field(lo, s, dims)
+        tris = sph.sph_surface_mesh(field, lo, s, 0.5)
+        out["surface"] = {"path": args.surface, "triangles": int(len(tris)),
+                          "vertices": export.write_obj(tris, args.surface)}
+    if args.image:
+        from paper_2403_11156_gb300 import export
+        lo, hi = d0["domain_min"], d0["domain_max"]
+        px = d0["radius"] / 2
+        w, h = int((hi[0] - lo[0]) / px), int((hi[1] - lo[1]) / px)
+        hm = g.sph_render_heightmap(lo[:2], (lo[0] + w * px, lo[1] + h * px), w, h, d0["radius"])
+        export.write_pgm(hm, px, args.image)
+        out["image"] = {"path": args.image, "width": w, "height": h}
     print(json.dumps(out))
     g.close()
 
