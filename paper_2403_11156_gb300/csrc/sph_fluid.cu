@@ -153,16 +153,18 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         for (int32_t dz = -R; dz <= R; ++dz) {
             const int32_t z = cz + dz;
             if (z < 0 || z >= sc.dims[2]) continue;
-            const float gz = gap(oz, dz);
+            const float gz = T > 1 ? gap(oz, dz) : 0.0f;
             for (int32_t dy = -R; dy <= R; ++dy) {
                 const int32_t y = cy + dy;
                 if (y < 0 || y >= sc.dims[1]) continue;
-                const float gy = gap(oy, dy);
-                const float g2 = fmaf(gy, gy, gz * gz);
-                if (g2 > cull2) continue;
                 int32_t x0 = cx - R, x1 = cx + R;
-                while (x0 < cx && fmaf(gap(ox, x0 - cx), gap(ox, x0 - cx), g2) > cull2) ++x0;
-                while (x1 > cx && fmaf(gap(ox, x1 - cx), gap(ox, x1 - cx), g2) > cull2) --x1;
+                if (T > 1) {   // with one lane the culling's registers cost more than it saves
+                    const float gy = gap(oy, dy);
+                    const float g2 = fmaf(gy, gy, gz * gz);
+                    if (g2 > cull2) continue;
+                    while (x0 < cx && fmaf(gap(ox, x0 - cx), gap(ox, x0 - cx), g2) > cull2) ++x0;
+                    while (x1 > cx && fmaf(gap(ox, x1 - cx), gap(ox, x1 - cx), g2) > cull2) --x1;
+                }
                 x0 = max(x0, 0);
                 x1 = min(x1, sc.dims[0] - 1);
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
