@@ -63,7 +63,8 @@ typedef enum sph_status {
 
 /* warm_start of the two DFSPH solves */
 #define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */
-#define SPH_WARM_PREVIOUS 1  /* half the previous step's kappa where the fluid compresses */
+#define SPH_WARM_PREVIOUS 1  /* a fraction (warm_start_fraction, default half) of the       */
+                             /* previous step's kappa where the fluid compresses          */
 #define SPH_WARM_LEARNED 2   /* density solve: per-particle network prediction (see       */
                              /* sph_set_mlp); divergence solve as SPH_WARM_PREVIOUS        */
 
@@ -120,6 +121,8 @@ typedef struct sph_scene_desc {
     int32_t pressure_solver;      /* SPH_SOLVER_*                                     */
     float eos_stiffness;          /* WCSPH k, Pa (> 0)                                */
     float eos_exponent;           /* WCSPH gamma (>= 1; 0 = 7)                        */
+    float warm_start_fraction;    /* SPH_WARM_PREVIOUS: fraction of the previous      */
+                                  /* step's stiffness (0..1; 0 = 0.5)                 */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

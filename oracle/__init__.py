@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("cg_max_iter", C.c_int32), ("pad_", C.c_int32),
         ("pressure_solver", C.c_int32), ("pad2_", C.c_int32),
         ("eos_stiffness", C.c_double), ("eos_exponent", C.c_double),
+        ("warm_start_fraction", C.c_double),
     ]
 
 
@@ -241,6 +242,7 @@ class Scene:
         p.pressure_solver = desc.get("pressure_solver", 0)
         p.eos_stiffness = desc.get("eos_stiffness", 0.0)
         p.eos_exponent = desc.get("eos_exponent", 7.0)
+        p.warm_start_fraction = desc.get("warm_start_fraction", 0.0)
         self.params = p
         self.nf = len(desc["fluid_x"])
         self.nb = len(desc["boundary_x"])

@@ -394,6 +394,7 @@ typedef struct {
     int32_t pressure_solver; /* 0 DFSPH, 1 WCSPH (equation of state, Sec. 3.4.1), 2 PCISPH  */
     int32_t pad2_;
     double eos_stiffness, eos_exponent;
+    double warm_start_fraction; /* fraction of the previous stiffness (0 = one half)       */
 } or_params;
 
 typedef struct {
@@ -882,6 +883,9 @@ void or_step(or_ctx *c, double dt_in)
 {
     double dt = dt_in > 0.0 ? dt_in : c->dt_next;
     double rho0 = c->p.rest_density;
+    /* warm starts take this fraction of the previous step's stiffness (a reading; 1/2 by
+     * default) */
+    double wf = c->p.warm_start_fraction > 0.0 ? c->p.warm_start_fraction : 0.5;
     int64_t nf = c->nf, nb = c->nb;
     c->stats[ST_DT] = dt;
 
@@ -899,7 +903,7 @@ void or_step(or_ctx *c, double dt_in)
             /* compresses (D rho/Dt > 0); elsewhere zero.                                   */
             for (int64_t i = 0; i < nf; ++i) {
                 double d = drho_dt(c, i);
-                kv[i] = d > 0.0 ? 0.5 * c->kappa_v_prev[i] / dt : 0.0;
+                kv[i] = d > 0.0 ? wf * c->kappa_v_prev[i] / dt : 0.0;
                 c->kappa_v[i] = kv[i];
             }
             apply_kappa(c, kv, dt);
@@ -959,7 +963,7 @@ void or_step(or_ctx *c, double dt_in)
         if (c->p.warm_start == 1) {
             /* half the previous step's total stiffness, stored as kappa dt^2 (a reading) */
             for (int64_t i = 0; i < nf; ++i)
-                c->kappa0[i] = dev[i] > 0.0 ? 0.5 * c->kappa_prev[i] / (dt * dt) : 0.0;
+                c->kappa0[i] = dev[i] > 0.0 ? wf * c->kappa_prev[i] / (dt * dt) : 0.0;
         } else if (c->p.warm_start == 2 && c->have_mlp) {
             warm_features(c, dt);
             const double *mu_f = c->mlp + OR_MLP_NW, *sd_f = mu_f + OR_F;

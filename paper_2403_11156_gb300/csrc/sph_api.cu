@@ -189,6 +189,7 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
+    if (!(d.warm_start_fraction >= 0.0f && d.warm_start_fraction <= 1.0f)) return bad("warm_start_fraction (0..1)");
     if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH &&
         d.pressure_solver != SPH_SOLVER_PCISPH)
         return bad("pressure_solver");
@@ -639,6 +640,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.warm = (wc || pci) ? 0 : d.warm_start;
         q.div_on = (d.divergence_solve && !wc && !pci) ? 1 : 0;
         q.pci_c = pci ? (float)pcisph_prototype(d.radius) : 0.0f;
+        q.warm_frac = d.warm_start_fraction > 0.0f ? d.warm_start_fraction : 0.5f;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;
         q.nbody = d.n_bodies;

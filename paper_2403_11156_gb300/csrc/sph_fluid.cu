@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         P.nnf[i] = min(nn_f, sc.cap_f);
         P.nnb[i] = min(nn_b, sc.cap_b);
         float kv0 = 0.0f;
-        if (gate && div_l > 0.0f) kv0 = 0.5f * P.kvprev_s[i] / c.st->dt;
+        if (gate && div_l > 0.0f) kv0 = sc.warm_frac * P.kvprev_s[i] / c.st->dt;
         P.kvsum[i] = kv0;
         set_w(P.pos_s, i, kv0 / rho);
     }
@@ -555,7 +555,8 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 }
 
 // Warm start of the constant-density solve: the predicted deviation rho* - rho0 with
-// v* gates half the previous step's stiffness (kept as kappa dt^2); the learned mode
+// v* gates a fraction (default half) of the previous step's stiffness (kept as kappa
+// dt^2); the learned mode
 // stores the network's input features instead (rho/rho0 - 1, dt Drho/Dt/rho0,
 // (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.
 template <int T>
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;
     if (sc.warm == 1) {
-        if (dev > 0.0f) k0 = 0.5f * P.kprev_s[i] / (dt * dt);
+        if (dev > 0.0f) k0 = sc.warm_frac * P.kprev_s[i] / (dt * dt);
     } else if (P.ctl->have_mlp) {
         k0 = dev > 0.0f ? 1.0f : 0.0f;   // gate; the network kernel replaces it
     }

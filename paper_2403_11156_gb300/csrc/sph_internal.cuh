@@ -53,6 +53,7 @@ struct SceneDev {
     int32_t solver;                   // 0 DFSPH, 1 WCSPH, 2 PCISPH
     float eos_k, eos_gamma;           // WCSPH equation of state
     float pci_c;                      // PCISPH prototype stiffness times dt^2
+    float warm_frac;                  // fraction of the previous stiffness warm-starting a solve
 };
 
 // Per-scene mutable state (device).

@@ -77,6 +77,7 @@ class SceneDesc(C.Structure):
         ("max_boundary_neighbors", C.c_int32), ("cg_tol", C.c_float), ("cg_max_iter", C.c_int32),
         ("lanes_per_particle", C.c_int32), ("pressure_solver", C.c_int32),
         ("eos_stiffness", C.c_float), ("eos_exponent", C.c_float),
+        ("warm_start_fraction", C.c_float),
     ]
 
 
@@ -261,6 +262,7 @@ def _make_desc(d, keep):
     s.pressure_solver = d.get("pressure_solver", 0)
     s.eos_stiffness = d.get("eos_stiffness", 0.0)
     s.eos_exponent = d.get("eos_exponent", 7.0)
+    s.warm_start_fraction = d.get("warm_start_fraction", 0.0)
     return s
 
 

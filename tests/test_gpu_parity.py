@@ -159,6 +159,23 @@ def test_one_step_fields(make, warm, visc, lanes):
     assert gs["div_err"] == pytest.approx(os_["div_err"], rel=1e-3, abs=1e-7)
 
 
+def test_warm_start_fraction_parity():
+    # a non-default warm-start fraction enters both warm starts the same way on both sides
+    d = forced(_small(warm_start=1, warm_start_fraction=0.75), 2, 3)
+    g = gpu_ctx(d)
+    o = oracle.Scene(d)
+    g.sph_step(DT)
+    x, v, _, _ = g.sph_read_state()
+    o.set_state(x, v, g.sph_read_field(sph.FIELD_KAPPA_PREV), g.sph_read_field(sph.FIELD_KAPPA_V_PREV))
+    g.sph_step(DT)
+    g.sph_synchronize(raise_on_error=False)
+    o.step(DT)
+    k_scale, v_tol = _field_tolerances(o, d, DT)
+    _assert_abs(g.sph_read_field(sph.FIELD_KAPPA0), o.get(oracle.KAPPA0), 1e-5 * k_scale, "kappa0")
+    _assert_abs(g.sph_read_field(sph.FIELD_KAPPA), o.get(oracle.KAPPA), 1e-5 * k_scale, "kappa")
+    _assert_abs(g.sph_read_state()[1], o.get(oracle.V), v_tol, "v")
+
+
 def test_iteration_counts_track_oracle():
     d = _c1()
     g = gpu_ctx(d)
