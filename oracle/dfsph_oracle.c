@@ -395,6 +395,8 @@ typedef struct {
     int32_t pad2_;
     double eos_stiffness, eos_exponent;
     double warm_start_fraction; /* fraction of the previous stiffness (0 = one half)       */
+    int32_t rigid_coupling;     /* 0 weak (body velocities fixed during the solves), 1 strong */
+    int32_t pad3_;
 } or_params;
 
 typedef struct {
@@ -859,6 +861,55 @@ int32_t or_visc_solve(or_ctx *c, double dt, const double *b, double *x)
     return (int32_t)c->stats[ST_CG_ITERS];
 }
 
+/* Strong rigid-fluid coupling (the paper's stated future work, Sec. 6, after its cited  */
+/* interlinked solver; a reading): every pressure application of the solves also pushes  */
+/* the bodies.  With the applied stiffness k (p/rho^2 = k/rho), the reaction of Eq.       */
+/* rigid_pressure_symmetric on boundary particle b is m Psi_b (k_i/rho_i) grad W_ib; its */
+/* sum over a body's particles changes the body's velocity by dt F / M and its angular    */
+/* velocity by dt I^-1 tau (world inertia of the step's orientation), and the boundary   */
+/* particle velocities follow before the next source term.  The sums are accumulated in  */
+/* body_force for output; the step's rigid integration then adds only gravity and the     */
+/* gyroscopic term.                                                                        */
+static void strong_impulse(or_ctx *c, const double *k, double dt)
+{
+    if (c->p.rigid_coupling != 1 || c->nbody == 0) return;
+    double *F = dalloc(6 * (size_t)c->nbody);
+    for (int64_t i = 0; i < c->nf; ++i) {
+        double kt = k[i] / c->rho[i];
+        for (int64_t t = c->fb.start[i]; t < c->fb.start[i + 1]; ++t) {
+            int64_t b = c->fb.idx[t];
+            int32_t kb = c->body[b];
+            if (kb < 0) continue;
+            double d[3], g[3], f[3];
+            diffxb(c, i, b, d);
+            or_gradW(d, c->h, g);
+            for (int a = 0; a < 3; ++a) f[a] = c->m * c->psi[b] * kt * g[a];
+            const or_body *B = &c->bodies[kb];
+            double r[3] = {c->xb[3 * b] - B->com[0], c->xb[3 * b + 1] - B->com[1], c->xb[3 * b + 2] - B->com[2]};
+            double *fb = F + 6 * kb;
+            for (int a = 0; a < 3; ++a) fb[a] += f[a];
+            fb[3] += r[1] * f[2] - r[2] * f[1];
+            fb[4] += r[2] * f[0] - r[0] * f[2];
+            fb[5] += r[0] * f[1] - r[1] * f[0];
+        }
+    }
+    for (int32_t kb = 0; kb < c->nbody; ++kb) {
+        or_body *B = &c->bodies[kb];
+        double *fb = F + 6 * kb, R[3][3], Iinv[3][3];
+        quat_to_R(B->quat, R);
+        for (int a = 0; a < 3; ++a)
+            for (int e = 0; e < 3; ++e) {
+                Iinv[a][e] = 0.0;
+                for (int q = 0; q < 3; ++q) Iinv[a][e] += R[a][q] / B->inertia[q] * R[e][q];
+            }
+        for (int a = 0; a < 3; ++a) B->vel[a] += dt * fb[a] / B->mass;
+        for (int a = 0; a < 3; ++a) B->omega[a] += dt * (Iinv[a][0] * fb[3] + Iinv[a][1] * fb[4] + Iinv[a][2] * fb[5]);
+        for (int a = 0; a < 6; ++a) c->body_force[6 * kb + a] += fb[a];
+    }
+    free(F);
+    set_boundary_from_bodies(c);
+}
+
 /* PCISPH stiffness of a prototype particle (the PCISPH reading of Alg. ppe_solver; the   */
 /* paper cites the method without restating it): with a full neighbourhood on the lattice */
 /* of spacing 2r, delta = 1 / (beta (|sum_j grad W_ij|^2 + sum_j |grad W_ij|^2)), beta =   */
@@ -891,6 +942,9 @@ void or_step(or_ctx *c, double dt_in)
 
     prepare(c);
 
+    int strong = c->p.rigid_coupling == 1;
+    for (int64_t k6 = 0; k6 < 6 * c->nbody; ++k6) c->body_force[k6] = 0.0;
+
     /* 4. divergence-free solve (Eq. velocity_source, Alg. ppe_solver, Jacobi updates) */
     for (int64_t i = 0; i < nf; ++i) c->kappa_v[i] = 0.0;
     int div_it = 0;
@@ -907,6 +961,7 @@ void or_step(or_ctx *c, double dt_in)
                 c->kappa_v[i] = kv[i];
             }
             apply_kappa(c, kv, dt);
+            strong_impulse(c, kv, dt);
         }
         for (;;) {
             if (div_it >= c->p.max_iter_divergence) break;
@@ -924,6 +979,7 @@ void or_step(or_ctx *c, double dt_in)
                 c->kappa_v[i] += kv[i];
             }
             apply_kappa(c, kv, dt);
+            strong_impulse(c, kv, dt);
             ++div_it;
             if (!((div_err > c->p.eta_divergence) || div_it < c->p.min_iter_divergence)) break;
         }
@@ -955,6 +1011,7 @@ void or_step(or_ctx *c, double dt_in)
             c->kappa[i] = k[i];
         }
         apply_kappa(c, k, dt);
+        strong_impulse(c, k, dt);
     }
     if (c->p.warm_start != 0 && !wcsph && !pcisph) {
         /* gate: predicted density deviation with v* before any pressure of this step */
@@ -983,6 +1040,7 @@ void or_step(or_ctx *c, double dt_in)
         free(dev);
         for (int64_t i = 0; i < nf; ++i) { k[i] = c->kappa0[i]; c->kappa[i] = k[i]; }
         apply_kappa(c, k, dt);
+        strong_impulse(c, k, dt);
     }
 
     /* 7. constant-density solve (Eq. density_source with rho* = rho - dt rho div v*).       */
@@ -1021,6 +1079,7 @@ void or_step(or_ctx *c, double dt_in)
             }
         }
         apply_kappa(c, k, dt);
+        strong_impulse(c, k, dt);
         ++dens_it;
         if (!((dens_err > c->p.eta_density) || dens_it < c->p.min_iter_density)) break;
     }
@@ -1033,7 +1092,8 @@ void or_step(or_ctx *c, double dt_in)
 
     /* 8a. boundary reaction (Sec. 3.5 Eq. rigid_pressure_symmetric) with the total applied  */
     /* kappa of this step; the fluid-side impulse is recorded for the antisymmetry pin.     */
-    for (int64_t k6 = 0; k6 < 6 * c->nbody; ++k6) c->body_force[k6] = 0.0;
+    if (!strong)
+        for (int64_t k6 = 0; k6 < 6 * c->nbody; ++k6) c->body_force[k6] = 0.0;
     for (int64_t i = 0; i < nf; ++i) {
         double kt = (c->kappa[i] + c->kappa_v[i]) / c->rho[i];
         double imp[3] = {0, 0, 0};
@@ -1048,7 +1108,7 @@ void or_step(or_ctx *c, double dt_in)
                 imp[a] -= dt * F[a];
             }
             int32_t kb = c->body[b];
-            if (kb >= 0) {
+            if (kb >= 0 && !strong) {
                 or_body *B = &c->bodies[kb];
                 double r[3] = {c->xb[3 * b] - B->com[0], c->xb[3 * b + 1] - B->com[1], c->xb[3 * b + 2] - B->com[2]};
                 double *bf = c->body_force + 6 * kb;
@@ -1070,7 +1130,9 @@ void or_step(or_ctx *c, double dt_in)
     for (int32_t kb = 0; kb < c->nbody; ++kb) {
         or_body *B = &c->bodies[kb];
         double *bf = c->body_force + 6 * kb;
-        for (int a = 0; a < 3; ++a) B->vel[a] += dt * (bf[a] / B->mass + c->p.gravity[a]);
+        /* strong coupling applied the fluid's impulses during the solves already */
+        const double fscale = strong ? 0.0 : 1.0;
+        for (int a = 0; a < 3; ++a) B->vel[a] += dt * (fscale * bf[a] / B->mass + c->p.gravity[a]);
         for (int a = 0; a < 3; ++a) B->com[a] += dt * B->vel[a];
         double R[3][3];
         quat_to_R(B->quat, R);
@@ -1087,9 +1149,9 @@ void or_step(or_ctx *c, double dt_in)
             }
         double Iwo[3], rhs[3];
         for (int a = 0; a < 3; ++a) Iwo[a] = Iw[a][0] * B->omega[0] + Iw[a][1] * B->omega[1] + Iw[a][2] * B->omega[2];
-        rhs[0] = bf[3] - (B->omega[1] * Iwo[2] - B->omega[2] * Iwo[1]);
-        rhs[1] = bf[4] - (B->omega[2] * Iwo[0] - B->omega[0] * Iwo[2]);
-        rhs[2] = bf[5] - (B->omega[0] * Iwo[1] - B->omega[1] * Iwo[0]);
+        rhs[0] = fscale * bf[3] - (B->omega[1] * Iwo[2] - B->omega[2] * Iwo[1]);
+        rhs[1] = fscale * bf[4] - (B->omega[2] * Iwo[0] - B->omega[0] * Iwo[2]);
+        rhs[2] = fscale * bf[5] - (B->omega[0] * Iwo[1] - B->omega[1] * Iwo[0]);
         for (int a = 0; a < 3; ++a) B->omega[a] += dt * (Iinv[a][0] * rhs[0] + Iinv[a][1] * rhs[1] + Iinv[a][2] * rhs[2]);
         double w = B->quat[0], qx = B->quat[1], qy = B->quat[2], qz = B->quat[3];
         double ox = B->omega[0], oy = B->omega[1], oz = B->omega[2];

@@ -23,6 +23,7 @@ import numpy as np
 VISC_NONE, VISC_EXPLICIT, VISC_XSPH, VISC_IMPLICIT = 0, 1, 2, 3
 WARM_ZERO, WARM_PREVIOUS, WARM_LEARNED = 0, 1, 2
 SOLVER_DFSPH, SOLVER_WCSPH, SOLVER_PCISPH = 0, 1, 2
+COUPLING_WEAK, COUPLING_STRONG = 0, 1
 
 
 def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, -9.81),
@@ -32,7 +33,7 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
            viscosity_mode=VISC_EXPLICIT, warm_start=WARM_PREVIOUS, divergence_solve=1,
            xsph_c=0.0, cg_tol=1e-4, cg_max_iter=500, max_fluid_neighbors=0,
            max_boundary_neighbors=0, cell_size=0.0, lanes_per_particle=0, pressure_solver=0,
-           eos_stiffness=0.0, eos_exponent=7.0, warm_start_fraction=0.0):
+           eos_stiffness=0.0, eos_exponent=7.0, warm_start_fraction=0.0, rigid_coupling=0):
     return dict(radius=float(radius), rest_density=float(rest_density),
                 viscosity=float(viscosity), gravity=tuple(float(g) for g in gravity),
                 domain_min=tuple(float(a) for a in domain_min),
@@ -49,7 +50,8 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
                 max_boundary_neighbors=int(max_boundary_neighbors),
                 cell_size=float(cell_size), lanes_per_particle=int(lanes_per_particle),
                 pressure_solver=int(pressure_solver), eos_stiffness=float(eos_stiffness),
-                eos_exponent=float(eos_exponent), warm_start_fraction=float(warm_start_fraction))
+                eos_exponent=float(eos_exponent), warm_start_fraction=float(warm_start_fraction),
+                rigid_coupling=int(rigid_coupling))
 
 
 def lattice_block(n, spacing, origin, jitter=0.0, rng=None):
@@ -175,6 +177,26 @@ def dam_break_pcisph(seed=1, n=(20, 20, 20), radius=0.01, box=0.8, **kw):
              min_iter_density=3)
     p.update(kw)
     return dam_break_small(seed=seed, n=n, radius=radius, box=box, **p)
+
+
+def body_in_fluid(seed=3, n=(14, 14, 14), radius=0.01, edge=0.06, density=300.0, compress=0.95,
+                  jitter=2e-4, **kw):
+    """A cube body (surface-sampled at 2r, given density) in the middle of a fluid lattice
+    block at spacing compress * 2r (slightly compressed, so the first step has pressure),
+    fluid particles closer than 1.1 spacings to the cube removed; no walls, no gravity
+    unless given."""
+    rng = np.random.default_rng(seed)
+    s = 2.0 * radius
+    fx = lattice_block(n, compress * s, (0.1, 0.1, 0.1), jitter, rng)
+    c = fx.astype(np.float64).mean(axis=0)
+    pts, body = cube_body(tuple(c), edge, s, density)
+    keep = np.any(np.abs(fx - c) > 0.5 * edge + WALL_GAP * s, axis=1)
+    ext = 0.2 + n[0] * s
+    defaults = dict(radius=radius, domain_min=(0.0, 0.0, 0.0), domain_max=(ext, ext, ext),
+                    gravity=(0.0, 0.0, 0.0), viscosity=0.0, viscosity_mode=VISC_NONE)
+    defaults.update(kw)
+    return _scene(fx[keep], pts, params(**defaults), boundary_body=np.zeros(len(pts), np.int32),
+                  bodies=[body])
 
 
 def dam_break_rigid(seed=2, n=(125, 98, 98), radius=0.005, tank=(2.0, 1.0, 1.0),
