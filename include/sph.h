@@ -61,6 +61,14 @@ typedef enum sph_status {
                              /* meets eta_density (min/max_iter_density); no divergence       */
                              /* solve, no warm start                                          */
 
+/* rigid_coupling */
+#define SPH_COUPLING_WEAK 0    /* body velocities fixed during the fluid solves (Sec. 3.5);  */
+                               /* the step's total reaction moves the bodies afterwards      */
+#define SPH_COUPLING_STRONG 1  /* every pressure application of the solves also pushes the  */
+                               /* bodies (dt F/M, dt I^-1 tau) and their boundary particles  */
+                               /* follow before the next source term (the paper's stated    */
+                               /* future work)                                               */
+
 /* warm_start of the two DFSPH solves */
 #define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */
 #define SPH_WARM_PREVIOUS 1  /* a fraction (warm_start_fraction, default half) of the       */
@@ -123,6 +131,7 @@ typedef struct sph_scene_desc {
     float eos_exponent;           /* WCSPH gamma (>= 1; 0 = 7)                        */
     float warm_start_fraction;    /* SPH_WARM_PREVIOUS: fraction of the previous      */
                                   /* step's stiffness (0..1; 0 = 0.5)                 */
+    int32_t rigid_coupling;       /* SPH_COUPLING_*                                   */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

@@ -76,7 +76,7 @@ struct sph_ctx {
     std::vector<int32_t> nbody_scene;
     int max_bodies = 0;
     bool any_moving = false, any_div = false, any_warm_div = false, any_warm = false,
-         any_learned = false, any_bodies = false, any_implicit = false, any_wcsph = false;
+         any_learned = false, any_bodies = false, any_implicit = false, any_wcsph = false, any_strong = false;
     Ptrs P{};
     SceneDev *d_scenes = nullptr;
 
@@ -190,6 +190,7 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
     if (!(d.warm_start_fraction >= 0.0f && d.warm_start_fraction <= 1.0f)) return bad("warm_start_fraction (0..1)");
+    if (d.rigid_coupling != SPH_COUPLING_WEAK && d.rigid_coupling != SPH_COUPLING_STRONG) return bad("rigid_coupling");
     if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH &&
         d.pressure_solver != SPH_SOLVER_PCISPH)
         return bad("pressure_solver");
@@ -474,12 +475,16 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         return device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
             run(c, q, na, [&] { launch_pass_a(P, solver, c->batch, q); });
             run(c, q, nb, [&] { launch_pass_b(P, solver, 0, c->batch, h, use, q); });
+            if (c->any_strong) run(c, q, "strong_coupling", [&] { launch_strong_update(P, q); });
         });
     };
 
     sph_status st;
     if (c->any_div) {
-        if (c->any_warm_div) run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, 0, 0, s); });
+        if (c->any_warm_div) {
+            run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, 0, 0, s); });
+            if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
+        }
         if ((st = loop(0)) != SPH_OK) return st;
     }
     run(c, s, "nonpressure", [&] { launch_nonpressure(P, s); });
@@ -498,8 +503,10 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     }
     // the warm-start pressure of the density solve, or the WCSPH equation-of-state pressure
     // (written by the non-pressure kernel), applied once
-    if (c->any_warm || c->any_wcsph)
+    if (c->any_warm || c->any_wcsph) {
         run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, 0, 0, s); });
+        if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
+    }
     if ((st = loop(1)) != SPH_OK) return st;
     if (c->any_bodies) {
         run(c, s, "body_force", [&] { launch_body_force(P, s); });
@@ -641,6 +648,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.div_on = (d.divergence_solve && !wc && !pci) ? 1 : 0;
         q.pci_c = pci ? (float)pcisph_prototype(d.radius) : 0.0f;
         q.warm_frac = d.warm_start_fraction > 0.0f ? d.warm_start_fraction : 0.5f;
+        q.strong = (d.rigid_coupling == SPH_COUPLING_STRONG && d.n_bodies > 0) ? 1 : 0;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;
         q.nbody = d.n_bodies;
@@ -684,6 +692,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         c->any_warm |= q.warm != 0;
         c->any_learned |= q.warm == 2;
         c->any_wcsph |= q.solver == SPH_SOLVER_WCSPH;
+        c->any_strong |= q.strong != 0;
         c->any_implicit |= d.viscosity_mode == 3;
     }
     if (NC >= ((int64_t)1 << 32) - 1 || NF >= ((int64_t)1 << 31) || (double)NF * cap_f > 4.0e10)

@@ -102,6 +102,14 @@ __global__ void k_step_begin(Ptrs P)
     st.max_nn_f = 0;
     st.max_nn_b = 0;
     st.maxv2 = 0.0f;
+    if (sc.strong)   // strongly coupled bodies accumulate the step's force during the solves
+        for (int k = 0; k < sc.nbody; ++k) {
+            BodyDev &B = P.bodies[sc.body_off + k];
+            for (int a = 0; a < 3; ++a) {
+                B.force[a] = 0.0;
+                B.torque[a] = 0.0;
+            }
+        }
 }
 
 // ------------------------------------------------------------------------------------
@@ -653,7 +661,8 @@ __global__ void k_step_end(Ptrs P)
         BodyDev &B = P.bodies[k];
         const SceneDev &sc = P.scenes[B.scene];
         const double dt = (double)P.st[B.scene].dt;
-        for (int a = 0; a < 3; ++a) B.vel[a] += dt * (B.force[a] / B.mass + (double)sc.g[a]);
+        const double fs = sc.strong ? 0.0 : 1.0;   // strong coupling applied the fluid's impulses already
+        for (int a = 0; a < 3; ++a) B.vel[a] += dt * (fs * B.force[a] / B.mass + (double)sc.g[a]);
         for (int a = 0; a < 3; ++a) B.com[a] += dt * B.vel[a];
         double w = B.quat[0], x = B.quat[1], y = B.quat[2], z = B.quat[3];
         double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
@@ -672,9 +681,9 @@ __global__ void k_step_end(Ptrs P)
         double o[3] = {B.omega[0], B.omega[1], B.omega[2]};
         double L[3];
         for (int a = 0; a < 3; ++a) L[a] = Iw[a][0] * o[0] + Iw[a][1] * o[1] + Iw[a][2] * o[2];
-        double rhs[3] = {B.torque[0] - (o[1] * L[2] - o[2] * L[1]),
-                         B.torque[1] - (o[2] * L[0] - o[0] * L[2]),
-                         B.torque[2] - (o[0] * L[1] - o[1] * L[0])};
+        double rhs[3] = {fs * B.torque[0] - (o[1] * L[2] - o[2] * L[1]),
+                         fs * B.torque[1] - (o[2] * L[0] - o[0] * L[2]),
+                         fs * B.torque[2] - (o[0] * L[1] - o[1] * L[0])};
         for (int a = 0; a < 3; ++a) B.omega[a] += dt * (Ii[a][0] * rhs[0] + Ii[a][1] * rhs[1] + Ii[a][2] * rhs[2]);
         double ox = B.omega[0], oy = B.omega[1], oz = B.omega[2];
         double dw = 0.5 * (-ox * x - oy * y - oz * z);

@@ -54,6 +54,7 @@ struct SceneDev {
     float eos_k, eos_gamma;           // WCSPH equation of state
     float pci_c;                      // PCISPH prototype stiffness times dt^2
     float warm_frac;                  // fraction of the previous stiffness warm-starting a solve
+    int32_t strong;                   // strong rigid coupling: bodies pushed during the solves
 };
 
 // Per-scene mutable state (device).
@@ -134,7 +135,10 @@ enum KernelId : uint32_t {
     KID_CG_AP = 26,
     KID_CG_XR = 27,
     KID_CG_P = 28,
-    KID_MLP_WARM = 29
+    KID_MLP_WARM = 29,
+    KID_BFORCE_INC = 30,
+    KID_BAPPLY = 31,
+    KID_BVEL = 32
 };
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
@@ -260,5 +264,6 @@ void launch_boundary_update(const Ptrs &P, cudaStream_t s);
 void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);
 void launch_body_force(const Ptrs &P, cudaStream_t s);
 void launch_body_reduce(const Ptrs &P, cudaStream_t s);
+void launch_strong_update(const Ptrs &P, cudaStream_t s);
 
 }  // namespace sph

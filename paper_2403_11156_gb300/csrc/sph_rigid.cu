@@ -87,16 +87,19 @@ __device__ double block_sum_d(double v, double *sh)
     return t;
 }
 
-// Force and torque of the fluid on each body of the scene for the step just solved (the
-// T lanes of a particle walk its T boundary sub-lists; the block sums add all lanes).
-template <int T>
+// Force and torque of the fluid on each body of the scene (the T lanes of a particle share
+// its boundary list; the block sums add all lanes), as per-block partials.  INC = false:
+// weakly coupled scenes, from the step's total applied stiffness after the solves;
+// INC = true: strongly coupled scenes, from the stiffness just applied (kappa/rho of the
+// current sweep).
+template <int T, bool INC>
 __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
-    kernel_enter(P.ctl, KID_BFORCE);
+    kernel_enter(P.ctl, INC ? KID_BFORCE_INC : KID_BFORCE);
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
-    if (sc.nbody == 0) return;  // uniform per block
+    if (sc.nbody == 0 || (sc.strong != 0) != INC) return;  // uniform per block
     const int64_t i = c.i, NF = P.NF;
     int nb = 0;
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     if (c.valid) {
         nb = P.nnb[i];
         pi = P.pos_s[i];
-        kt = (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
+        kt = INC ? pi.w : (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
     }
     // which bodies this block's particles touch (most blocks touch none, or only walls):
     // untouched bodies get zero partials without a reduction
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
     const int body = blockIdx.x / 6, a = blockIdx.x % 6;
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];
+    if (sc.strong) return;   // strongly coupled bodies take their forces during the solves
     const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first;
     double t = 0.0;
 #pragma unroll 4
@@ -171,7 +175,87 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
     }
 }
 
+// Strong coupling: one block per body sums the partials of the stiffness just applied (in
+// block order), adds them to the step's force and torque and applies the impulse,
+// v += dt F / M, omega += dt I^-1 tau (world inertia of the step's orientation).
+__global__ void __launch_bounds__(256) k_body_apply(Ptrs P)
+{
+    __shared__ double sh[8];
+    __shared__ double s_f[6];
+    kernel_enter(P.ctl, KID_BAPPLY);
+    const int body = blockIdx.x;
+    BodyDev &B = P.bodies[body];
+    const SceneDev &sc = P.scenes[B.scene];
+    if (!sc.strong) return;
+    for (int a = 0; a < 6; ++a) {
+        const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first;
+        double t = 0.0;
+        for (int q = threadIdx.x; q < sc.tblk_count; q += 256) t += part[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < 8; ++w) tot += sh[w];
+            s_f[a] = tot;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double dt = (double)P.st[B.scene].dt;
+    const double w = B.quat[0], x = B.quat[1], y = B.quat[2], z = B.quat[3];
+    const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                            {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                            {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+    for (int a = 0; a < 3; ++a) {
+        B.force[a] += s_f[a];
+        B.torque[a] += s_f[3 + a];
+        B.vel[a] += dt * s_f[a] / B.mass;
+    }
+    for (int a = 0; a < 3; ++a) {
+        double d = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            double ii = 0.0;
+            for (int q = 0; q < 3; ++q) ii += R[a][q] / B.inertia[q] * R[e][q];
+            d += ii * s_f[3 + e];
+        }
+        B.omega[a] += dt * d;
+    }
+}
+
+// Strong coupling: the boundary particles of strongly coupled bodies follow the updated
+// body velocities, v_b = v + omega x (x_b - com) (grid order).
+__global__ void __launch_bounds__(kBlock) k_boundary_vel(Ptrs P)
+{
+    kernel_enter(P.ctl, KID_BVEL);
+    const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
+    if (!sc.strong || sc.nbody == 0) return;
+    const int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
+    if (local >= sc.nb) return;
+    const int64_t b = sc.b_off + local;
+    const int32_t k = P.bbody_s[b];
+    if (k < 0) return;
+    const BodyDev &B = P.bodies[sc.body_off + k];
+    const float4 pb = P.bpos_s[b];
+    const double rx = (double)pb.x - B.com[0], ry = (double)pb.y - B.com[1], rz = (double)pb.z - B.com[2];
+    P.bvel_s[b] = make_float4((float)(B.vel[0] + (B.omega[1] * rz - B.omega[2] * ry)),
+                              (float)(B.vel[1] + (B.omega[2] * rx - B.omega[0] * rz)),
+                              (float)(B.vel[2] + (B.omega[0] * ry - B.omega[1] * rx)), 0.0f);
+}
+
 }  // namespace
+
+void launch_strong_update(const Ptrs &P, cudaStream_t s)
+{
+    if (!P.ntblk || !P.nbodies_total) return;
+#define SPH_L(T) k_body_force<T, true><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+    k_body_apply<<<P.nbodies_total, 256, 0, s>>>(P);
+    if (P.nbblk) k_boundary_vel<<<P.nbblk, kBlock, 0, s>>>(P);
+}
 
 void launch_boundary_update(const Ptrs &P, cudaStream_t s)
 {
@@ -184,7 +268,7 @@ void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s)
 void launch_body_force(const Ptrs &P, cudaStream_t s)
 {
     if (!P.ntblk) return;
-#define SPH_L(T) k_body_force<T><<<P.ntblk, kBlock, 0, s>>>(P)
+#define SPH_L(T) k_body_force<T, false><<<P.ntblk, kBlock, 0, s>>>(P)
     SPH_BY_LANES(P, SPH_L);
 #undef SPH_L
 }

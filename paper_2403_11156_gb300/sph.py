@@ -44,7 +44,8 @@ KERNEL_IDS = {i + 1: n for i, n in enumerate([
     "rank_gather_fluid", "rank_gather_boundary", "density_alpha", "div_pass_a", "dens_pass_a",
     "div_pass_b", "dens_pass_b", "div_warm_pass_b", "dens_warm_pass_b", "nonpressure", "warm_density",
     "advect", "step_end", "set_dt", "boundary_update", "boundary_psi", "body_force", "body_reduce",
-    "cg_init", "cg_ap", "cg_xr", "cg_p", "mlp_warm"])}
+    "cg_init", "cg_ap", "cg_xr", "cg_p", "mlp_warm", "body_force_inc", "body_apply",
+    "boundary_vel"])}
 
 
 class SphError(RuntimeError):
@@ -77,7 +78,7 @@ class SceneDesc(C.Structure):
         ("max_boundary_neighbors", C.c_int32), ("cg_tol", C.c_float), ("cg_max_iter", C.c_int32),
         ("lanes_per_particle", C.c_int32), ("pressure_solver", C.c_int32),
         ("eos_stiffness", C.c_float), ("eos_exponent", C.c_float),
-        ("warm_start_fraction", C.c_float),
+        ("warm_start_fraction", C.c_float), ("rigid_coupling", C.c_int32),
     ]
 
 
@@ -263,6 +264,7 @@ def _make_desc(d, keep):
     s.eos_stiffness = d.get("eos_stiffness", 0.0)
     s.eos_exponent = d.get("eos_exponent", 7.0)
     s.warm_start_fraction = d.get("warm_start_fraction", 0.0)
+    s.rigid_coupling = d.get("rigid_coupling", 0)
     return s
 
 
