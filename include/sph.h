@@ -204,7 +204,10 @@ sph_status sph_synchronize(sph_ctx *ctx);
 /* Copy the state of one scene out, in original particle order.  Any pointer may be NULL.
  * x, v: [n_fluid][3]; rho, pressure: [n_fluid] (pressure p = kappa rho of the last
  * constant-density solve, Sec. 3.3 Eq. pressure_acceleration; zero before the first
- * step).  on_device != 0: the pointers are device memory.  Synchronises. */
+ * step).  on_device == 0: host memory, synchronises; 1: device memory, synchronises;
+ * 2: device memory, only enqueued on the context's stream (order later work after it with
+ * an event on that stream), so a caller can copy a step's result out while the next step
+ * runs. */
 sph_status sph_read_state(sph_ctx *ctx, int32_t scene, float *x, float *v, float *rho,
                           float *pressure, int32_t on_device);
 
@@ -233,7 +236,7 @@ sph_status sph_write_state(sph_ctx *ctx, int32_t scene, const float *x, const fl
 #define SPH_FIELD_FEATURES 14    /* float [n][4]: warm-start network inputs            */
 #define SPH_FIELD_KAPPA0 15      /* float: density warm-start stiffness of the last step */
 sph_status sph_read_field(sph_ctx *ctx, int32_t scene, int32_t field, void *out,
-                          int32_t on_device);
+                          int32_t on_device);   /* on_device as for sph_read_state */
 
 /* Statistics of one scene (synchronises). */
 sph_status sph_get_stats(sph_ctx *ctx, int32_t scene, sph_stats *out);

@@ -1213,7 +1213,7 @@ sph_status sph_read_state(sph_ctx *c, int32_t scene, float *x, float *v, float *
     if ((st = read_into(c, scene, 101, v, 12 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 102, rho, 4 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 103, pressure, 4 * nf, false, on_device)) != SPH_OK) return st;
-    CK(cudaStreamSynchronize(c->stream));
+    if (on_device != 2) CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
 
@@ -1241,7 +1241,7 @@ sph_status sph_read_field(sph_ctx *c, int32_t scene, int32_t field, void *out, i
     default: return fail(c, SPH_EINVAL, "unknown field %d", field);
     }
     if ((st = read_into(c, scene, field, out, bytes, boundary, on_device)) != SPH_OK) return st;
-    CK(cudaStreamSynchronize(c->stream));
+    if (on_device != 2) CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
 

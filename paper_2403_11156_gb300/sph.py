@@ -338,12 +338,13 @@ class Context:
                                                rho.ctypes.data, p.ctypes.data, 0))
         return x, v, rho, p
 
-    def sph_read_state_device(self, scene, x=None, v=None, rho=None, pressure=None):
-        """Write into caller-owned device buffers (torch tensors or raw pointers)."""
+    def sph_read_state_device(self, scene, x=None, v=None, rho=None, pressure=None, sync=True):
+        """Write into caller-owned device buffers (torch tensors or raw pointers); with
+        sync=False the copy is only enqueued on the context's stream."""
         def ptr(t):
             return None if t is None else (t.data_ptr() if hasattr(t, "data_ptr") else int(t))
         _check(self.ctx, load().sph_read_state(self.ctx, scene, ptr(x), ptr(v), ptr(rho),
-                                               ptr(pressure), 1))
+                                               ptr(pressure), 1 if sync else 2))
 
     def sph_write_state(self, scene=0, x=None, v=None, kappa_prev=None, kappa_v_prev=None):
         def arr(a, shape):

@@ -114,3 +114,17 @@ def test_read_state_device_matches_host():
     hx, _, _, hp = g.sph_read_state()
     np.testing.assert_array_equal(x.cpu().numpy(), hx)
     np.testing.assert_array_equal(p.cpu().numpy(), hp)
+
+
+def test_enqueue_only_read_matches_synchronous_read():
+    import torch
+    d = _small()
+    g = gpu_ctx(d)
+    g.sph_steps(3, DT)
+    n = len(d["fluid_x"])
+    x = torch.empty((n, 3), device="cuda")
+    g.sph_read_state_device(0, x=x, sync=False)
+    g.sph_synchronize()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy(), g.sph_read_state()[0])
+
