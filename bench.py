@@ -128,7 +128,8 @@ def learned_vs_plain():
     """Train the warm-start network on the GPU from the solver's own states (200k samples
     from 500 steps of seeded 0.5M-1.2M-particle dam breaks) and compare the zero,
     previous-step and learned warm starts on the 8k-particle dam break (100 steps, fixed
-    dt = 4e-4 s) at the 0.1 % tolerance and at 0.001 %."""
+    dt = 4e-4 s) at the 0.1 % tolerance and at 0.001 %, and on the 1.2M-particle rigid dam
+    break (200 steps from rest, CFL dt, 0.1 %)."""
     import time as _t
     from paper_2403_11156_gb300 import scenes, warmstart
     t = _t.perf_counter()
@@ -142,6 +143,14 @@ def learned_vs_plain():
     for tag, eta in (("eta_1e-3", 1e-3), ("eta_1e-5", 1e-5)):
         desc = scenes.dam_break_small(eta_density=eta, eta_divergence=eta)
         out[tag] = warmstart.compare_warm_starts(desc, params, steps=100)
+    out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(scenes.dam_break_rigid(), params, steps=200)
+    for res in (out["eta_1e-3"], out["dam_break_1.2M_rigid"]):
+        p, l = res["previous"], res["learned"]
+        res["learned_over_previous"] = {
+            "density_iteration_ratio": p["density_iters_per_step"] / l["density_iters_per_step"],
+            "solver_iteration_ratio": (p["density_iters_per_step"] + p["divergence_iters_per_step"]) /
+                                      (l["density_iters_per_step"] + l["divergence_iters_per_step"]),
+            "time_ratio": p["ms_per_step"] / l["ms_per_step"]}
     return out
 
 

@@ -743,6 +743,13 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         ok &= dalloc(c, P.cg_dots, 2 * (size_t)std::max(std::max(nfblk, ntblk), 1));
     }
     ok &= dalloc(c, P.mlp_w, SPH_MLP_PARAMS);
+    if (c->any_learned) {
+        int64_t nl = 0;
+        for (int32_t k = 0; k < n; ++k)
+            if (c->scenes[k].warm == 2) nl += c->scenes[k].nf;
+        P.nlearned = nl;
+        ok &= dalloc(c, P.mlp_rows, std::max<int64_t>(nl, 1));
+    }
     P.scan_tiles = scan_tiles_for(NC);
     ok &= dalloc(c, P.scan_status, std::max(P.scan_tiles, 1));
     if (!ok) return bail(fail(c, SPH_ENOMEM, "device allocation failed"));

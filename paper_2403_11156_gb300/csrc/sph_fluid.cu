@@ -86,6 +86,7 @@ __global__ void k_step_begin(Ptrs P)
     if (s == 0) {
         P.ctl->passb_counter = 0;
         P.ctl->loop_guard = 0;
+        P.ctl->mlp_n = 0;
     }
     if (s >= P.nscenes) return;
     const SceneDev &sc = P.scenes[s];
@@ -583,10 +584,25 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
         D = drho_dt_lane<kBatch, T>(P, sc, i, c.s, pi, vi, P.vel_c);
     }
     D = group_sum<T>(D);
-    if (!c.valid || c.s != 0) return;
+    const bool own = c.valid && c.s == 0;
     const float dt = c.st->dt;
     const float rho = vi.w;
     const float dev = fmaf(dt, D, rho - sc.rho0);
+    // learned mode: the gated particles (predicted compression) are appended to the rows
+    // of the network kernel, one atomic per warp (the whole warp is converged here)
+    if (sc.warm == 2) {
+        const bool gated = own && dev > 0.0f && P.ctl->have_mlp;
+        const unsigned m = __ballot_sync(0xffffffffu, gated);
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (m != 0) {
+            const int lead = __ffs(m) - 1;
+            if (lane == lead) base = atomicAdd(&P.ctl->mlp_n, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, lead);
+        }
+        if (gated) P.mlp_rows[base + __popc(m & ((1u << lane) - 1u))] = make_int2((int)i, P.tblk_scene[blockIdx.x]);
+    }
+    if (!own) return;
     // the network's inputs are recorded in both warm-start modes (the previous-step mode
     // produces the training data)
     const float kref = 9.81f * sc.h;
@@ -597,11 +613,8 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     f.w = P.kprev_s[i] / (dt * dt) / kref;
     reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;
-    if (sc.warm == 1) {
-        if (dev > 0.0f) k0 = sc.warm_frac * P.kprev_s[i] / (dt * dt);
-    } else if (P.ctl->have_mlp) {
-        k0 = dev > 0.0f ? 1.0f : 0.0f;   // gate; the network kernel replaces it
-    }
+    if (sc.warm == 1 && dev > 0.0f) k0 = sc.warm_frac * P.kprev_s[i] / (dt * dt);
+    // learned mode: zero here, the network kernel fills the gated rows
     P.k0[i] = k0;
     P.ksum[i] = k0;
     set_w(P.pos_s, i, k0 / rho);

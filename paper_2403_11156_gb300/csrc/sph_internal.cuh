@@ -103,6 +103,8 @@ struct Control {
     int32_t have_mlp;                 // warm-start network loaded
     uint32_t trace_n, trace_cap;      // device trace: stamps written / capacity
     unsigned long long *trace;        // (globaltimer << 8 | kernel id) per launch, or null
+    int32_t mlp_n;                    // rows the warm-start network runs on this step
+    int32_t pad1;
 };
 
 // Kernel identifiers of the device trace.
@@ -200,6 +202,8 @@ struct Ptrs {
     double *cg_dots;                  // per-block partials [max(nfblk, ntblk)][2]
     // network
     float *mlp_w;                     // device parameter block (float)
+    int2 *mlp_rows;                   // [nlearned] gated (particle, scene) rows of the step
+    int64_t nlearned;                 // fluid particles of learned-warm-start scenes
 };
 
 // ------------------------------------------------------------------ grid (sph_grid.cu)

@@ -44,9 +44,9 @@ constexpr uint32_t kSmVec = 32768;     // b1, b2, w3 (float[64] each)
 constexpr uint32_t kSmBar = 33536;     // mbarrier
 constexpr uint32_t kSmTmem = 33544;    // tensor-memory address
 constexpr uint32_t kSmUsed = 33600;
-// requested dynamic shared memory: caps residency at 3 CTAs per SM, so 3 x 128
-// tensor-memory columns never exceed the SM's 512
-constexpr uint32_t kSmRequest = 72 * 1024;
+// requested dynamic shared memory: caps residency at 4 CTAs per SM (4 x (52 + 1) KB of the
+// SM's 228 KB; a fifth would need 265), so 4 x 128 tensor-memory columns never exceed 512
+constexpr uint32_t kSmRequest = 52 * 1024;
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kWaitLimit = 1u << 20;
 
@@ -65,9 +65,15 @@ __device__ __forceinline__ void store8(unsigned char *tile, uint32_t r, uint32_t
     *reinterpret_cast<uint4 *>(tile + tc::tile_offset(r, k0, K)) = q;
 }
 
-// The network for the CTA's 128 rows; thread t owns row t.  f: standardised features.
-// Returns the standardised output y.  *ok is cleared if a tensor-core wait gave up.
-__device__ float mlp_tile(const float *__restrict__ w, const float f[4], unsigned char *sm, bool *ok)
+// One CTA runs the network over 128-row tiles: it allocates its tensor memory and stages
+// the weights once, then walks tiles tile0, tile0 + stride, ... < ntiles.  Thread t owns
+// row t of a tile; rows.load(tile, t, f) fills the standardised features of that row
+// (false: padding, features zero) and rows.store(tile, t, y) receives the standardised
+// output y of every valid row.  Returns false if a tensor-core wait gave up (the caller
+// flags the error).
+template <class Rows>
+__device__ bool mlp_tiles(const float *__restrict__ w, unsigned char *sm, int64_t tile0, int64_t ntiles,
+                          int64_t stride, Rows &rows)
 {
     const int t = threadIdx.x, warp = t >> 5;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
@@ -77,11 +83,10 @@ __device__ float mlp_tile(const float *__restrict__ w, const float f[4], unsigne
     float *w3 = b2 + kH;
     if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
     if (t == 0) tc::mbar_init(bar, 1);
-    // layer-1 operand A: row t = (f0..f3, 0 x 12); B1 row n = W1[n][0..3], 0 x 12
+    // layer-1 operand A: row t = (f0..f3, 0 x 12), the zero half written once; B1 row n =
+    // W1[n][0..3], 0 x 12; W2 as the layer-2 operand B
     {
-        float v[8] = {f[0], f[1], f[2], f[3], 0.f, 0.f, 0.f, 0.f};
         const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        store8(sm + kSmA1, t, 0, 16, v);
         store8(sm + kSmA1, t, 8, 16, z);
         if (t < kH) {
             float u[8] = {w[kOffW1 + t * kF + 0], w[kOffW1 + t * kF + 1], w[kOffW1 + t * kF + 2],
@@ -100,120 +105,186 @@ __device__ float mlp_tile(const float *__restrict__ w, const float f[4], unsigne
             store8(sm + kSmB2, n, kc, kH, u);
         }
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
+    const float b3 = w[kOffB3];
     const uint32_t idesc = tc::idesc_bf16_f32(128, kH);
     const uint32_t sbase = tc::smem_addr(sm);
-    if (t == 0) {
-        // D1[128 x 64] = A1[128 x 16] B1[64 x 16]^T: one K = 16 step
-        tc::mma_bf16(tmem, tc::smem_desc(sbase + kSmA1, 128, 256), tc::smem_desc(sbase + kSmB1, 128, 256), idesc, 0);
-        tc::mma_commit(bar);
-    }
-    bool good = tc::mbar_wait_bounded(bar, 0, kWaitLimit);
-    tc::fence_after_sync();
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    // hidden layer 1: bias, GELU, BF16 -> layer-2 operand A (row t)
+    bool good = true;
+    uint32_t failed_parity = 1;
+    uint32_t tmem = 0;
+    for (int64_t tile = tile0; tile < ntiles; tile += stride) {
+        float f[4];
+        const bool valid = rows.load(tile, t, f);
+        {
+            const float v[8] = {f[0], f[1], f[2], f[3], 0.f, 0.f, 0.f, 0.f};
+            store8(sm + kSmA1, t, 0, 16, v);
+        }
+        // orders this tile's operand writes before the MMA and the previous tile's
+        // tensor-memory reads before the accumulators are overwritten; a failed wait of the
+        // previous tile ends the walk on every thread
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(good)) { failed_parity = 1; break; }
+        tc::fence_after_sync();
+        tmem = *tmem_slot;
+        if (t == 0) {
+            // D1[128 x 64] = A1[128 x 16] B1[64 x 16]^T: one K = 16 step
+            tc::mma_bf16(tmem, tc::smem_desc(sbase + kSmA1, 128, 256), tc::smem_desc(sbase + kSmB1, 128, 256),
+                         idesc, 0);
+            tc::mma_commit(bar);
+        }
+        good = tc::mbar_wait_bounded(bar, 0, kWaitLimit);
+        tc::fence_after_sync();
+        // hidden layer 1: bias, GELU, BF16 -> layer-2 operand A (row t)
 #pragma unroll
-    for (int c = 0; c < kH / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(tmem + lane_base + c * 16, v);
+        for (int c = 0; c < kH / 16; ++c) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + c * 16, v);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = gelu(v[k] + b1[c * 16 + k]);
-        store8(sm + kSmA2, t, c * 16, kH, v);
-        store8(sm + kSmA2, t, c * 16 + 8, kH, v + 8);
+            for (int k = 0; k < 16; ++k) v[k] = gelu(v[k] + b1[c * 16 + k]);
+            store8(sm + kSmA2, t, c * 16, kH, v);
+            store8(sm + kSmA2, t, c * 16 + 8, kH, v + 8);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(good)) { failed_parity = 0; break; }
+        tc::fence_after_sync();
+        if (t == 0) {
+            // D2[128 x 64] = A2[128 x 64] W2^T in four K = 16 steps (two core matrices each)
+#pragma unroll
+            for (int k = 0; k < kH / 16; ++k)
+                tc::mma_bf16(tmem + kH, tc::smem_desc(sbase + kSmA2 + k * 256, 128, 1024),
+                             tc::smem_desc(sbase + kSmB2 + k * 256, 128, 1024), idesc, k > 0 ? 1u : 0u);
+            tc::mma_commit(bar);
+        }
+        good = tc::mbar_wait_bounded(bar, 1, kWaitLimit);
+        tc::fence_after_sync();
+        float y = b3;
+#pragma unroll
+        for (int c = 0; c < kH / 16; ++c) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + kH + c * 16, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) y = fmaf(w3[c * 16 + k], gelu(v[k] + b2[c * 16 + k]), y);
+        }
+        if (valid) rows.store(tile, t, y);
     }
-    tc::fence_proxy_async();
     tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) {
-        // D2[128 x 64] = A2[128 x 64] W2^T in four K = 16 steps (two core matrices each)
-#pragma unroll
-        for (int k = 0; k < kH / 16; ++k)
-            tc::mma_bf16(tmem + kH, tc::smem_desc(sbase + kSmA2 + k * 256, 128, 1024),
-                         tc::smem_desc(sbase + kSmB2 + k * 256, 128, 1024), idesc, k > 0 ? 1u : 0u);
-        tc::mma_commit(bar);
-    }
-    good = tc::mbar_wait_bounded(bar, 1, kWaitLimit) && good;
-    tc::fence_after_sync();
-    float y = w[kOffB3];
-#pragma unroll
-    for (int c = 0; c < kH / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(tmem + lane_base + kH + c * 16, v);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) y = fmaf(w3[c * 16 + k], gelu(v[k] + b2[c * 16 + k]), y);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
+    good = __syncthreads_and(good);
     if (!good && t == 0) {
         // an MMA did not report completion: give it one more bounded wait before the
         // tensor memory is released
-        tc::mbar_wait_bounded(bar, 1, kWaitLimit);
+        tc::mbar_wait_bounded(bar, failed_parity, kWaitLimit);
     }
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
-    *ok = good;
-    return y;
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(*tmem_slot, kTmemCols);
+    return good;
 }
 
-// Standalone forward on standardised features [n][4] -> y [n].
+// Rows of the standalone forward: standardised features [n][4] -> y [n].
+struct DenseRows {
+    const float4 *feat;
+    float *y;
+    int64_t n;
+    __device__ bool load(int64_t tile, int t, float f[4]) const
+    {
+        const int64_t i = tile * 128 + t;
+        if (i >= n) {
+            f[0] = f[1] = f[2] = f[3] = 0.f;
+            return false;
+        }
+        const float4 q = feat[i];
+        f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
+        return true;
+    }
+    __device__ void store(int64_t tile, int t, float out) const { y[tile * 128 + t] = out; }
+};
+
 __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ w, const float4 *__restrict__ feat,
                                                      int64_t n, float *__restrict__ y, int *err)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    if (i < n) {
-        const float4 q = feat[i];
-        f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
-    }
-    bool ok;
-    const float out = mlp_tile(w, f, sm, &ok);
-    if (i < n) y[i] = out;
-    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    DenseRows rows{feat, y, n};
+    const int64_t ntiles = (n + 127) / 128;
+    if (!mlp_tiles(w, sm, blockIdx.x, ntiles, gridDim.x, rows) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
-// Learned warm start inside a step: features from k_warm_density (raw), its gate in k0.
-__global__ void __launch_bounds__(128) k_mlp_warm(Ptrs P)
-{
-    extern __shared__ __align__(1024) unsigned char sm[];
-    kernel_enter(P.ctl, KID_MLP_WARM);
-    const int32_t s = P.fblk_scene[blockIdx.x];
-    const SceneDev &sc = P.scenes[s];
-    if (sc.warm != 2 || !P.ctl->have_mlp) return;  // uniform per block, before any allocation
-    const int64_t local = (int64_t)(blockIdx.x - sc.fblk_first) * kBlock + threadIdx.x;
-    const bool valid = local < sc.nf;
-    const int64_t i = sc.f_off + local;
-    const float *w = P.mlp_w;
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    if (valid) {
-        const float4 q = reinterpret_cast<const float4 *>(P.feat)[i];
+// Rows of the learned warm start: the compact list of gated particles (particle, scene)
+// that k_warm_density appended; raw features standardised here, the output scaled to
+// kappa0 = max((y std_y + mean_y) 9.81 h, 0) and written with its pressure slot.
+struct GatedRows {
+    const int2 *list;
+    const float4 *feat;
+    const SceneDev *scenes;
+    float *k0, *ksum;
+    float4 *pos_s;
+    const float4 *vel_c;
+    const float *w;
+    int32_t n;
+    int32_t i, s;   // the row's particle and scene
+    __device__ bool load(int64_t tile, int t, float f[4])
+    {
+        const int64_t r = tile * 128 + t;
+        if (r >= n) {
+            f[0] = f[1] = f[2] = f[3] = 0.f;
+            return false;
+        }
+        const int2 e = list[r];
+        i = e.x;
+        s = e.y;
+        const float4 q = feat[i];
         f[0] = (q.x - w[kOffMuF + 0]) / w[kOffSdF + 0];
         f[1] = (q.y - w[kOffMuF + 1]) / w[kOffSdF + 1];
         f[2] = (q.z - w[kOffMuF + 2]) / w[kOffSdF + 2];
         f[3] = (q.w - w[kOffMuF + 3]) / w[kOffSdF + 3];
+        return true;
     }
-    bool ok;
-    const float y = mlp_tile(w, f, sm, &ok);
-    if (valid) {
-        const float gate = P.k0[i];
-        const float k0 = gate > 0.0f ? fmaxf((y * w[kOffSdY] + w[kOffMuY]) * 9.81f * sc.h, 0.0f) : 0.0f;
-        P.k0[i] = k0;
-        P.ksum[i] = k0;
-        reinterpret_cast<float *>(P.pos_s + i)[3] = k0 / P.vel_c[i].w;
+    __device__ void store(int64_t, int, float y) const
+    {
+        const float k = fmaxf((y * w[kOffSdY] + w[kOffMuY]) * 9.81f * scenes[s].h, 0.0f);
+        k0[i] = k;
+        ksum[i] = k;
+        reinterpret_cast<float *>(pos_s + i)[3] = k / vel_c[i].w;
     }
-    if (!ok && threadIdx.x == 0) atomicExch(&P.ctl->error, 4);
+};
+
+// Learned warm start inside a step: a persistent grid over the gated rows (their count
+// is known only on the device).
+__global__ void __launch_bounds__(128) k_mlp_warm(Ptrs P)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    kernel_enter(P.ctl, KID_MLP_WARM);
+    const int32_t n = P.ctl->mlp_n;
+    const int64_t ntiles = (n + 127) / 128;
+    if (!P.ctl->have_mlp || (int64_t)blockIdx.x >= ntiles) return;  // uniform per block
+    GatedRows rows{P.mlp_rows, reinterpret_cast<const float4 *>(P.feat), P.scenes, P.k0, P.ksum, P.pos_s, P.vel_c,
+                   P.mlp_w, n, 0, 0};
+    if (!mlp_tiles(P.mlp_w, sm, blockIdx.x, ntiles, gridDim.x, rows) && threadIdx.x == 0)
+        atomicExch(&P.ctl->error, 4);
+}
+
+// Resident CTAs of the network kernels per SM: the shared-memory request caps it, so that
+// their tensor-memory columns (128 each) never exceed the SM's 512.
+constexpr int kMlpCtasPerSm = 4;
+
+int mlp_grid(int64_t tiles)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            nsm = 1;
+    }
+    const int64_t g = (int64_t)nsm * kMlpCtasPerSm;
+    return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
 }
 
 }  // namespace
 
 void launch_mlp_warm(const Ptrs &P, cudaStream_t s)
 {
-    k_mlp_warm<<<P.nfblk, kBlock, kSmRequest, s>>>(P);
+    k_mlp_warm<<<mlp_grid((P.nlearned + 127) / 128), 128, kSmRequest, s>>>(P);
 }
 
 cudaError_t mlp_prepare_kernels()
@@ -233,9 +304,7 @@ extern "C" sph_status sph_mlp_forward(const float *params, const float *features
     if (n < 0 || (n > 0 && (!params || !features || !y || !error))) return SPH_EINVAL;
     if (n == 0) return SPH_OK;
     if (mlp_prepare_kernels() != cudaSuccess) return SPH_ECUDA;
-    const int64_t blocks = (n + 127) / 128;
-    if (blocks > 0x7fffffff) return SPH_EINVAL;
-    k_mlp_forward<<<(unsigned)blocks, 128, kSmRequest, (cudaStream_t)stream>>>(
+    k_mlp_forward<<<mlp_grid((n + 127) / 128), 128, kSmRequest, (cudaStream_t)stream>>>(
         params, reinterpret_cast<const float4 *>(features), n, y, reinterpret_cast<int *>(error));
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }

@@ -39,7 +39,7 @@ def _bf16_reference(p, f):
     return a2 @ W3 + b3
 
 
-@pytest.mark.parametrize("n", [1000, 128, 77])
+@pytest.mark.parametrize("n", [1000, 128, 77, 200_003])
 def test_forward_matches_oracle(n):
     import torch
     rng = np.random.default_rng(n)

@@ -75,3 +75,38 @@ def test_learned_mode_runs(trained):
     for mode in ("zero", "previous", "learned"):
         assert res[mode]["final_error"] <= 1e-3 or res[mode]["density_iters_per_step"] >= 100
         assert res[mode]["density_iters_per_step"] >= 2
+
+
+def test_network_rows_are_the_gated_particles(trained):
+    """The in-step network runs on the compact list of gated particles: every particle the
+    gate opens gets exactly the standalone forward of its standardised features (scaled to
+    kappa0), every other particle kappa0 = 0, and a second context reproduces the field
+    bit for bit although the list's order depends on the warps' atomics."""
+    import torch
+    params, _ = trained
+    d = forced(scenes.dam_break_small(warm_start=scenes.WARM_LEARNED), 1, 2)
+    k0s = []
+    for _ in range(2):
+        g = gpu_ctx(d)
+        g.sph_set_mlp(params)
+        for _ in range(4):
+            g.sph_step(4e-4)
+        g.sph_synchronize(raise_on_error=False)
+        k0s.append(g.sph_read_field(sph.FIELD_KAPPA0))
+        feat = g.sph_read_field(sph.FIELD_FEATURES)
+    np.testing.assert_array_equal(k0s[0], k0s[1])
+    k0 = k0s[0]
+    p = np.asarray(params, np.float32)
+    nw = 4545
+    mu, sd, mu_y, sd_y = p[nw:nw + 4], p[nw + 4:nw + 8], p[nw + 8], p[nw + 9]
+    fs = torch.tensor((feat - mu) / sd, dtype=torch.float32, device="cuda")
+    n = len(fs)
+    y = torch.full((n,), np.nan, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert sph.sph_mlp_forward(torch.tensor(p, device="cuda"), fs, n, y, err) == sph.SPH_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    want = np.maximum((y.cpu().numpy().astype(np.float64) * sd_y + mu_y) * 9.81 * 4.0 * d["radius"], 0.0)
+    on = k0 > 0
+    assert on.sum() > 100 and (~on).sum() > 0
+    np.testing.assert_allclose(k0[on], want[on], rtol=1e-5, atol=1e-6 * np.abs(want).max())
