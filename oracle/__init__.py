@@ -58,6 +58,7 @@ class Params(C.Structure):
         ("eos_stiffness", C.c_double), ("eos_exponent", C.c_double),
         ("warm_start_fraction", C.c_double),
         ("rigid_coupling", C.c_int32), ("pad3_", C.c_int32),
+        ("learned_fraction", C.c_double),
     ]
 
 
@@ -244,6 +245,7 @@ class Scene:
         p.eos_stiffness = desc.get("eos_stiffness", 0.0)
         p.eos_exponent = desc.get("eos_exponent", 7.0)
         p.warm_start_fraction = desc.get("warm_start_fraction", 0.0)
+        p.learned_fraction = desc.get("learned_fraction", 0.0)
         p.rigid_coupling = desc.get("rigid_coupling", 0)
         self.params = p
         self.nf = len(desc["fluid_x"])

@@ -397,6 +397,7 @@ typedef struct {
     double warm_start_fraction; /* fraction of the previous stiffness (0 = one half)       */
     int32_t rigid_coupling;     /* 0 weak (body velocities fixed during the solves), 1 strong */
     int32_t pad3_;
+    double learned_fraction;    /* fraction of the network's stiffness applied (0 = 0.6)   */
 } or_params;
 
 typedef struct {
@@ -1029,10 +1030,13 @@ void or_step(or_ctx *c, double dt_in)
             for (int64_t i = 0; i < nf; ++i)
                 for (int a = 0; a < 4; ++a) fn[4 * i + a] = (c->feat[4 * i + a] - mu_f[a]) / sd_f[a];
             or_mlp_forward(c->mlp, nf, fn, y);
+            /* like the previous-step start, only a fraction of the predicted stiffness is
+               applied (a reading: the full prediction overshoots where it errs high) */
             double kref = 9.81 * c->h;
+            double lf = c->p.learned_fraction > 0.0 ? c->p.learned_fraction : 0.6;
             for (int64_t i = 0; i < nf; ++i) {
                 double kk = (y[i] * sd_y + mu_y) * kref;
-                c->kappa0[i] = (dev[i] > 0.0 && kk > 0.0) ? kk : 0.0;
+                c->kappa0[i] = (dev[i] > 0.0 && kk > 0.0) ? lf * kk : 0.0;
             }
             free(fn);
             free(y);

@@ -71,3 +71,40 @@ def test_overfit_small_set(oracle_lib):
         loss, g = oracle_lib.mlp_loss_grad(w, f, t)
         oracle_lib.adam_step(w, m, v, g, it, lr=3e-3)
     assert loss < 0.02 * l0
+
+
+def test_learned_fraction_scales_kappa0():
+    """The learned warm start applies a fraction of the network's stiffness: kappa0 at a
+    fraction f is f times kappa0 at f = 1, the default fraction is 0.6, and at f = 1 kappa0
+    is the network's de-standardised output (9.81 h units) on the gated particles."""
+    import oracle
+    from paper_2403_11156_gb300 import scenes
+    rng = np.random.default_rng(7)
+    nw = oracle.mlp_nweights()
+    p = np.zeros(oracle.mlp_nparam())
+    p[:nw] = rng.normal(scale=0.3, size=nw)
+    p[nw:nw + 4] = (0.0, 0.0, 1.0, 1.0)          # feature means
+    p[nw + 4:nw + 8] = (1e-3, 1e-3, 0.1, 1.0)    # feature stds
+    p[nw + 8], p[nw + 9] = 1.0, 0.5               # label mean, std (kappa0 mostly > 0)
+    base = oracle.Scene(scenes.dam_break_small(n=(8, 8, 8)))
+    for _ in range(3):
+        base.step(4e-4)
+    x, v = base.get(oracle.X), base.get(oracle.V)
+    k0 = {}
+    for f in (1.0, 0.3, 0.0):
+        d = scenes.dam_break_small(n=(8, 8, 8), warm_start=scenes.WARM_LEARNED, learned_fraction=f)
+        o = oracle.Scene(d)
+        o.set_mlp(p)
+        o.set_state(x, v)                          # the same state for every fraction
+        o.step(4e-4)
+        k0[f] = o.get(oracle.KAPPA0)
+        if f == 1.0:
+            feat = o.get(oracle.FEAT)
+            h = 4.0 * d["radius"]
+    on = k0[1.0] > 0
+    assert on.sum() >= 10
+    np.testing.assert_allclose(k0[0.3], 0.3 * k0[1.0], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(k0[0.0], 0.6 * k0[1.0], rtol=1e-12, atol=0)
+    y = oracle.mlp_forward(p, (feat - p[nw:nw + 4]) / p[nw + 4:nw + 8])
+    want = (y * p[nw + 9] + p[nw + 8]) * 9.81 * h
+    np.testing.assert_allclose(k0[1.0][on], want[on], rtol=1e-12)
