@@ -73,8 +73,10 @@ typedef enum sph_status {
 #define SPH_WARM_ZERO 0      /* kappa starts at zero                                       */
 #define SPH_WARM_PREVIOUS 1  /* a fraction (warm_start_fraction, default half) of the       */
                              /* previous step's kappa where the fluid compresses          */
-#define SPH_WARM_LEARNED 2   /* density solve: per-particle network prediction (see       */
-                             /* sph_set_mlp); divergence solve as SPH_WARM_PREVIOUS        */
+#define SPH_WARM_LEARNED 2   /* density solve: a fraction (learned_fraction) of a          */
+                             /* per-particle network prediction (see sph_set_mlp) where   */
+                             /* the fluid compresses; divergence solve as                 */
+                             /* SPH_WARM_PREVIOUS                                          */
 
 /* A rigid body (Sec. 3.5, two-way weak coupling; Sec. 4.1 initial pose and velocity). */
 typedef struct sph_rigid_desc {
@@ -132,6 +134,8 @@ typedef struct sph_scene_desc {
     float warm_start_fraction;    /* SPH_WARM_PREVIOUS: fraction of the previous      */
                                   /* step's stiffness (0..1; 0 = 0.5)                 */
     int32_t rigid_coupling;       /* SPH_COUPLING_*                                   */
+    float learned_fraction;       /* SPH_WARM_LEARNED: fraction of the network's      */
+                                  /* predicted stiffness applied (0..1; 0 = 0.6)      */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

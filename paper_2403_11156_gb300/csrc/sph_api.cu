@@ -190,6 +190,7 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
         d.lanes_per_particle != 4)
         return bad("lanes_per_particle (0, 1, 2 or 4)");
     if (!(d.warm_start_fraction >= 0.0f && d.warm_start_fraction <= 1.0f)) return bad("warm_start_fraction (0..1)");
+    if (!(d.learned_fraction >= 0.0f && d.learned_fraction <= 1.0f)) return bad("learned_fraction (0..1)");
     if (d.rigid_coupling != SPH_COUPLING_WEAK && d.rigid_coupling != SPH_COUPLING_STRONG) return bad("rigid_coupling");
     if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH &&
         d.pressure_solver != SPH_SOLVER_PCISPH)
@@ -648,6 +649,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.div_on = (d.divergence_solve && !wc && !pci) ? 1 : 0;
         q.pci_c = pci ? (float)pcisph_prototype(d.radius) : 0.0f;
         q.warm_frac = d.warm_start_fraction > 0.0f ? d.warm_start_fraction : 0.5f;
+        q.learned_frac = d.learned_fraction > 0.0f ? d.learned_fraction : 0.6f;
         q.strong = (d.rigid_coupling == SPH_COUPLING_STRONG && d.n_bodies > 0) ? 1 : 0;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;

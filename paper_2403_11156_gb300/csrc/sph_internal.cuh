@@ -55,6 +55,8 @@ struct SceneDev {
     float pci_c;                      // PCISPH prototype stiffness times dt^2
     float warm_frac;                  // fraction of the previous stiffness warm-starting a solve
     int32_t strong;                   // strong rigid coupling: bodies pushed during the solves
+    float learned_frac;               // fraction of the network's stiffness warm-starting it
+    int32_t pad_l;
 };
 
 // Per-scene mutable state (device).

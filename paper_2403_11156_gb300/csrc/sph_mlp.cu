@@ -1,11 +1,13 @@
 // sph_mlp.cu -- learned warm start of the constant-density solve (this library's
 // addition; the paper has no learned component): a per-particle network
 //   y = W3 gelu(W2 gelu(W1 f + b1) + b2) + b3,   f in R^4, hidden 64, exact-erf GELU,
-// on standardised features f = (raw - mean) / std; the prediction kappa0 =
-// max((y std_y + mean_y) 9.81 h, 0) applies where the fluid compresses.  Both hidden
-// layers run on the tcgen05 tensor cores (BF16 operands, FP32 accumulation in tensor
-// memory) for a tile of 128 particles per CTA; the 64-wide output dot product runs on the
-// CUDA cores while the second layer's accumulators are read back.
+// on standardised features f = (raw - mean) / std; a fraction of the prediction,
+// kappa0 = frac max((y std_y + mean_y) 9.81 h, 0), applies where the fluid compresses.
+// Both hidden layers run on the tcgen05 tensor cores (BF16 operands, FP32 accumulation
+// in tensor memory) for tiles of 128 rows; the 64-wide output dot product runs on the
+// CUDA cores while the second layer's accumulators are read back.  The kernels are
+// persistent: a CTA allocates its tensor memory and stages the weights once, then walks
+// its tiles.  Inside a step only the particles whose gate is open are rows.
 //
 // Parameter block (float, length kMlpParams): W1[64][4], b1[64], W2[64][64], b2[64],
 // W3[64], b3, feature mean[4], feature std[4], label mean, label std.
@@ -212,7 +214,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ w
 
 // Rows of the learned warm start: the compact list of gated particles (particle, scene)
 // that k_warm_density appended; raw features standardised here, the output scaled to
-// kappa0 = max((y std_y + mean_y) 9.81 h, 0) and written with its pressure slot.
+// kappa0 = f max((y std_y + mean_y) 9.81 h, 0) with the scene's fraction f, and written
+// with its pressure slot.
 struct GatedRows {
     const int2 *list;
     const float4 *feat;
@@ -242,7 +245,8 @@ struct GatedRows {
     }
     __device__ void store(int64_t, int, float y) const
     {
-        const float k = fmaxf((y * w[kOffSdY] + w[kOffMuY]) * 9.81f * scenes[s].h, 0.0f);
+        const SceneDev &sc = scenes[s];
+        const float k = sc.learned_frac * fmaxf((y * w[kOffSdY] + w[kOffMuY]) * 9.81f * sc.h, 0.0f);
         k0[i] = k;
         ksum[i] = k;
         reinterpret_cast<float *>(pos_s + i)[3] = k / vel_c[i].w;

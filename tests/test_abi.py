@@ -47,7 +47,8 @@ def _bad(**kw):
     dict(min_iter_density=-1), dict(max_iter_divergence=-3), dict(viscosity_mode=7), dict(warm_start=9),
     dict(dt_max=0.0), dict(max_fluid_neighbors=5000), dict(cell_size=0.01),
     dict(lanes_per_particle=3), dict(lanes_per_particle=-1), dict(lanes_per_particle=8),
-    dict(warm_start_fraction=1.5), dict(warm_start_fraction=-0.1), dict(pressure_solver=3),
+    dict(warm_start_fraction=1.5), dict(warm_start_fraction=-0.1), dict(learned_fraction=1.01),
+    dict(learned_fraction=-1.0), dict(pressure_solver=3),
     dict(pressure_solver=1, eos_stiffness=0.0),
     dict(fluid_x=np.full((3, 3), np.nan, np.float32)),
     dict(fluid_x=np.zeros((0, 3), np.float32)),

@@ -106,7 +106,7 @@ def test_network_rows_are_the_gated_particles(trained):
     assert sph.sph_mlp_forward(torch.tensor(p, device="cuda"), fs, n, y, err) == sph.SPH_OK
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    want = np.maximum((y.cpu().numpy().astype(np.float64) * sd_y + mu_y) * 9.81 * 4.0 * d["radius"], 0.0)
+    want = 0.6 * np.maximum((y.cpu().numpy().astype(np.float64) * sd_y + mu_y) * 9.81 * 4.0 * d["radius"], 0.0)
     on = k0 > 0
     assert on.sum() > 100 and (~on).sum() > 0
     np.testing.assert_allclose(k0[on], want[on], rtol=1e-5, atol=1e-6 * np.abs(want).max())
