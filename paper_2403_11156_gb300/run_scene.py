@@ -9,7 +9,9 @@ wcsph (the 8k dam break under the equation-of-state solver).
 without it a step is one CUDA-graph launch.  --lanes sets the threads per particle of the
 neighbour sweeps (1, 2, 4; 0 chooses by size).  --surface / --image write the post-processing
 results of scene 0 after the steps: the iso-surface of the fluid (OBJ) and a shaded
-height map seen from above (PGM).
+height map seen from above (PGM).  --warm picks the warm start of the solves (zero,
+previous, learned); the learned one loads a parameter block (--mlp, .npy) or, without one,
+first trains the network on 50k solver states of a seeded 0.5M-particle dam break.
 """
 from __future__ import annotations
 
@@ -26,6 +28,7 @@ WORKLOADS = {
     "batch": lambda: scenes.batch_dam_break(),
     "wcsph": lambda: [scenes.dam_break_wcsph()],
 }
+WARM = {"zero": scenes.WARM_ZERO, "previous": scenes.WARM_PREVIOUS, "learned": scenes.WARM_LEARNED}
 
 
 def main():
@@ -38,12 +41,27 @@ def main():
     ap.add_argument("--surface", default=None, help="write the fluid's iso-surface (OBJ) of scene 0 here")
     ap.add_argument("--image", default=None, help="write a height-map image (PGM) of scene 0 here")
     ap.add_argument("--grid", type=float, default=0.0, help="surface grid spacing (default: r)")
+    ap.add_argument("--warm", default=None, choices=sorted(WARM), help="warm start (default: the workload's)")
+    ap.add_argument("--mlp", default=None, help="network parameter block (.npy) for --warm learned")
     args = ap.parse_args()
     build.build()
+    params = None
+    if args.warm == "learned":
+        import numpy as np
+        if args.mlp:
+            params = np.load(args.mlp)
+        else:
+            from paper_2403_11156_gb300 import warmstart
+            f, y = warmstart.generate_dataset(50_000, 50, n_scenes=1, size_range=(5e5, 5e5))
+            params, _ = warmstart.train(f, y, epochs=30)
     descs = WORKLOADS[args.scene]()
     for d in descs:
         d["lanes_per_particle"] = args.lanes
+        if args.warm:
+            d["warm_start"] = WARM[args.warm]
     g = sph.Context(descs, torch_allocator=False)
+    if params is not None:
+        g.sph_set_mlp(params)
     g.sph_set_mode(graph=not args.eager, timing=False)
     t = time.perf_counter()
     g.sph_steps(args.steps, args.dt)
