@@ -143,7 +143,10 @@ def learned_vs_plain():
     for tag, eta in (("eta_1e-3", 1e-3), ("eta_1e-5", 1e-5)):
         desc = scenes.dam_break_small(eta_density=eta, eta_divergence=eta)
         out[tag] = warmstart.compare_warm_starts(desc, params, steps=100)
-    out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(scenes.dam_break_rigid(), params, steps=200)
+    big = scenes.dam_break_rigid()
+    out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(big, params, steps=200)
+    for mode in out["dam_break_1.2M_rigid"].values():
+        mode["particle_steps_per_s"] = len(big["fluid_x"]) / (mode["ms_per_step"] / 1000.0)
     for res in (out["eta_1e-3"], out["dam_break_1.2M_rigid"]):
         p, l = res["previous"], res["learned"]
         res["learned_over_previous"] = {
@@ -151,6 +154,41 @@ def learned_vs_plain():
             "solver_iteration_ratio": (p["density_iters_per_step"] + p["divergence_iters_per_step"]) /
                                       (l["density_iters_per_step"] + l["divergence_iters_per_step"]),
             "time_ratio": p["ms_per_step"] / l["ms_per_step"]}
+    return out, params
+
+
+def batched_learned(params, steps=200):
+    """The 64-scene batch (as in batched_throughput) with the previous-step and the learned
+    warm starts: 200 graph steps after 5 warm-up steps (the first steps from rest sit at the
+    minimum iteration counts under either start); ms per step and mean iterations."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    out = {}
+    for name, mode in (("previous", scenes.WARM_PREVIOUS), ("learned", scenes.WARM_LEARNED)):
+        ds = scenes.batch_dam_break()
+        for d in ds:
+            d["warm_start"] = mode
+        nf = sum(len(d["fluid_x"]) for d in ds)
+        stream = torch.cuda.Stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with sph.Context(ds, stream=stream) as g:
+            if mode == scenes.WARM_LEARNED:
+                g.sph_set_mlp(params)
+            g.sph_steps(5, 0.0)
+            g.sph_synchronize(raise_on_error=False)
+            s0 = [g.sph_get_stats(k) for k in range(len(ds))]
+            a.record(stream)
+            g.sph_steps(steps, 0.0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            s1 = [g.sph_get_stats(k) for k in range(len(ds))]
+        dens = [(y["total_dens_iters"] - x["total_dens_iters"]) / steps for x, y in zip(s0, s1)]
+        div = [(y["total_div_iters"] - x["total_div_iters"]) / steps for x, y in zip(s0, s1)]
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": nf / (ms / 1000.0),
+                     "mean_density_iters": float(np.mean(dens)), "max_density_iters": float(np.max(dens)),
+                     "mean_divergence_iters": float(np.mean(div))}
+    out["time_ratio"] = out["previous"]["ms_per_step"] / out["learned"]["ms_per_step"]
     return out
 
 
@@ -462,7 +500,9 @@ def main():
         post = post_processing(g, desc, stream)
     learned = None
     if rank == 0 and not args.no_learned:
-        learned = learned_vs_plain()
+        learned, params = learned_vs_plain()
+        if not args.no_batched:
+            learned["batched_64_scenes"] = batched_learned(params)
     batched = None
     if not args.no_batched:
         batched = batched_throughput(rank=rank, world=world, barrier=barrier)

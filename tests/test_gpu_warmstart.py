@@ -110,3 +110,23 @@ def test_network_rows_are_the_gated_particles(trained):
     on = k0 > 0
     assert on.sum() > 100 and (~on).sum() > 0
     np.testing.assert_allclose(k0[on], want[on], rtol=1e-5, atol=1e-6 * np.abs(want).max())
+
+
+def test_learned_batch_equals_single(trained):
+    """Learned scenes batched with a previous-step scene (their gated rows share the
+    network's tiles) step bit-identically to each scene alone."""
+    params, _ = trained
+    ds = [scenes.dam_break_small(seed=3, warm_start=scenes.WARM_LEARNED),
+          scenes.dam_break_small(seed=4, n=(17, 5, 9), box=0.5),
+          scenes.dam_break_small(seed=5, n=(12, 14, 10), warm_start=scenes.WARM_LEARNED, learned_fraction=0.8)]
+    batch = gpu_ctx(ds)
+    batch.sph_set_mlp(params)
+    batch.sph_steps(6, 4e-4)
+    for k, d in enumerate(ds):
+        single = gpu_ctx(d)
+        single.sph_set_mlp(params)
+        single.sph_steps(6, 4e-4)
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w)
+        np.testing.assert_array_equal(batch.sph_read_field(sph.FIELD_KAPPA0, k), single.sph_read_field(sph.FIELD_KAPPA0))
+        assert batch.sph_get_stats(k)["total_dens_iters"] == single.sph_get_stats()["total_dens_iters"]
