@@ -44,3 +44,24 @@ def oracle_step(desc, dt, steps=1):
     for _ in range(steps):
         o.step(dt)
     return o
+
+
+def field_tolerances(o, d, dt):
+    """Per-particle scales of the one-step field comparison: kappa against alpha rho0 / dt^2
+    (a 1e-5 rho0 error in rho*), velocities against the change such an error implies."""
+    alpha = o.get(oracle.ALPHA)
+    rho = o.get(oracle.RHO)
+    rho0 = d["rest_density"]
+    k_scale = alpha * rho0 / dt ** 2
+    v_tol = 1e-5 * rho0 * np.sqrt(np.maximum(alpha, 0) / rho) / dt
+    return k_scale, v_tol
+
+
+def assert_abs(gpu, ref, tol, what):
+    """Every row of gpu within its per-particle tol (plus 1e-5 of the row's magnitude)."""
+    gpu = np.asarray(gpu, np.float64).reshape(len(tol), -1)
+    ref = np.asarray(ref, np.float64).reshape(len(tol), -1)
+    e = np.abs(gpu - ref).max(axis=1) / (tol + 1e-5 * np.abs(ref).max(axis=1) + 1e-30)
+    k = int(np.argmax(e))
+    assert e.max() <= 1.0, "%s: worst %.3g of tolerance at %d (gpu %r ref %r tol %.3g)" % (
+        what, e.max(), k, gpu[k], ref[k], tol[k])

@@ -19,7 +19,7 @@ import pytest
 import oracle
 from paper_2403_11156_gb300 import scenes, sph
 
-from gpu_util import assert_rel, forced, gpu_ctx, oracle_step
+from gpu_util import assert_abs as _assert_abs, assert_rel, field_tolerances as _field_tolerances, forced, gpu_ctx, oracle_step
 
 pytestmark = pytest.mark.gpu
 
@@ -107,24 +107,6 @@ def test_density_alpha_psi(make, lanes):
     assert_rel(g.sph_read_field(sph.FIELD_PSI), o.get(oracle.PSI), 1e-5, what="psi")
     assert_rel(g.sph_read_field(sph.FIELD_RHO), o.get(oracle.RHO), 1e-5, what="rho")
     assert_rel(g.sph_read_field(sph.FIELD_ALPHA), o.get(oracle.ALPHA), 1e-5, what="alpha")
-
-
-def _field_tolerances(o, d, dt):
-    alpha = o.get(oracle.ALPHA)
-    rho = o.get(oracle.RHO)
-    rho0 = d["rest_density"]
-    k_scale = alpha * rho0 / dt ** 2
-    v_tol = 1e-5 * rho0 * np.sqrt(np.maximum(alpha, 0) / rho) / dt
-    return k_scale, v_tol
-
-
-def _assert_abs(gpu, ref, tol, what):
-    gpu = np.asarray(gpu, np.float64).reshape(len(tol), -1)
-    ref = np.asarray(ref, np.float64).reshape(len(tol), -1)
-    e = np.abs(gpu - ref).max(axis=1) / (tol + 1e-5 * np.abs(ref).max(axis=1) + 1e-30)
-    k = int(np.argmax(e))
-    assert e.max() <= 1.0, "%s: worst %.3g of tolerance at %d (gpu %r ref %r tol %.3g)" % (
-        what, e.max(), k, gpu[k], ref[k], tol[k])
 
 
 @pytest.mark.parametrize("lanes", LANES)
