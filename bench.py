@@ -111,6 +111,8 @@ class ClockSampler:
 
 
 def cpu_baseline(desc, steps=2):
+    """The oracle on the host cores: `steps` steps of the full workload with every core
+    (OpenMP), and one step of the reference arm's scaled copy on one thread."""
     import oracle
     oracle.build()
     o = oracle.Scene(desc)
@@ -119,9 +121,23 @@ def cpu_baseline(desc, steps=2):
         o.step(0.0)
     el = time.perf_counter() - t
     n = len(desc["fluid_x"])
-    return {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    d1 = reference_sample()
+    o1 = oracle.Scene(d1)
+    oracle.set_num_threads(1)
+    try:
+        t = time.perf_counter()
+        o1.step(0.0)
+        el1 = time.perf_counter() - t
+    finally:
+        oracle.set_num_threads(cores)
+    n1 = len(d1["fluid_x"])
+    return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d oracle steps of the full %d-particle workload from its initial state "
-                      "(FP64, OpenMP, %.1f s)" % (steps, n, el)}
+                      "(FP64, OpenMP, %.1f s)" % (steps, n, el),
+            "single_thread": {"value": n1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": "1 oracle step of a %d-particle scaled copy of the workload "
+                                        "from its initial state (FP64, %.1f s)" % (n1, el1)}}
 
 
 def learned_vs_plain():

@@ -114,6 +114,8 @@ def lib():
         L.or_dt_next.restype = C.c_double
         L.or_dt_next.argtypes = [C.c_void_p]
         L.or_num_threads.restype = C.c_int32
+        L.or_set_num_threads.argtypes = [C.c_int32]
+        L.or_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -211,6 +213,11 @@ def adam_step(w, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    lib().or_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------------------------- scene
