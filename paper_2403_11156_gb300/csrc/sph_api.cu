@@ -63,6 +63,8 @@ struct PendingTime {
 struct sph_ctx {
     cudaStream_t stream = nullptr;       // caller's stream (may be the legacy default)
     cudaStream_t cap0 = nullptr, cap1 = nullptr;  // capture streams
+    cudaStream_t side = nullptr;         // branch of the step that runs beside the fluid sort
+    cudaEvent_t fork = nullptr, join = nullptr;
     sph_allocator alloc{};
     bool use_alloc = false;
     std::vector<Alloc> allocs;
@@ -422,18 +424,27 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
 {
     const Ptrs &P = c->P;
     run(c, s, "step_begin", [&] { launch_step_begin(P, s); });
+    // Moving bodies: their boundary particles' update, grid order and Psi touch nothing
+    // the fluid sort does (each sort has its own scan state), so they run as a branch on
+    // the side stream beside it (a parallel branch of the captured graph) and join before
+    // the density sweep.
     if (c->any_moving) {
-        run(c, s, "boundary_update", [&] { launch_boundary_update(P, s); });
-        run(c, s, "bsort_key_hist", [&] { launch_key_hist(P, SORT_BOUNDARY, s); });
-        run(c, s, "bsort_scan", [&] { launch_scan_cells(P, SORT_BOUNDARY, s); });
-        run(c, s, "bsort_scatter", [&] { launch_scatter(P, SORT_BOUNDARY, s); });
-        run(c, s, "bsort_rank_gather", [&] { launch_rank_gather(P, SORT_BOUNDARY, s); });
-        run(c, s, "boundary_psi", [&] { launch_boundary_psi(P, 1, s); });
+        cudaStream_t b = c->side;
+        CK(cudaEventRecord(c->fork, s));
+        CK(cudaStreamWaitEvent(b, c->fork, 0));
+        run(c, b, "boundary_update", [&] { launch_boundary_update(P, b); });
+        run(c, b, "bsort_key_hist", [&] { launch_key_hist(P, SORT_BOUNDARY, b); });
+        run(c, b, "bsort_scan", [&] { launch_scan_cells(P, SORT_BOUNDARY, b); });
+        run(c, b, "bsort_scatter", [&] { launch_scatter(P, SORT_BOUNDARY, b); });
+        run(c, b, "bsort_rank_gather", [&] { launch_rank_gather(P, SORT_BOUNDARY, b); });
+        run(c, b, "boundary_psi", [&] { launch_boundary_psi(P, 1, b); });
+        CK(cudaEventRecord(c->join, b));
     }
     run(c, s, "sort_key_hist", [&] { launch_key_hist(P, SORT_FLUID, s); });
     run(c, s, "sort_scan", [&] { launch_scan_cells(P, SORT_FLUID, s); });
     run(c, s, "sort_scatter", [&] { launch_scatter(P, SORT_FLUID, s); });
     run(c, s, "sort_rank_gather", [&] { launch_rank_gather(P, SORT_FLUID, s); });
+    if (c->any_moving) CK(cudaStreamWaitEvent(s, c->join, 0));
     run(c, s, "density_alpha", [&] { launch_density_alpha(P, s); });
 
     // A device-controlled loop: in capture mode a conditional while node whose body is
@@ -754,6 +765,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     }
     P.scan_tiles = scan_tiles_for(NC);
     ok &= dalloc(c, P.scan_status, std::max(P.scan_tiles, 1));
+    ok &= dalloc(c, P.bscan_status, std::max(P.scan_tiles, 1));
     if (!ok) return bail(fail(c, SPH_ENOMEM, "device allocation failed"));
     P.scenes = c->d_scenes;
     P.st = st;
@@ -765,7 +777,10 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
 
     // streams used only for capture
     if (cudaStreamCreateWithFlags(&c->cap0, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap1, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&c->cap1, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(c, SPH_ECUDA, "stream creation failed"));
 
     // ---- upload
@@ -877,6 +892,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= cudaMemsetAsync(P.cell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.bcell_count, 0, sizeof(uint32_t) * NC, s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.scan_status, 0, sizeof(uint64_t) * std::max(P.scan_tiles, 1), s) == cudaSuccess;
+    ok &= cudaMemsetAsync(P.bscan_status, 0, sizeof(uint64_t) * std::max(P.scan_tiles, 1), s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.kprev_c, 0, sizeof(float) * NF, s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.kvprev_c, 0, sizeof(float) * NF, s) == cudaSuccess;
     ok &= cudaMemsetAsync(P.ksum, 0, sizeof(float) * NF, s) == cudaSuccess;
@@ -1479,6 +1495,9 @@ void sph_destroy(sph_ctx *c)
     if (c->trace) cudaFree(c->trace);
     if (c->cap0) cudaStreamDestroy(c->cap0);
     if (c->cap1) cudaStreamDestroy(c->cap1);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     delete c;
 }
 

@@ -119,7 +119,7 @@ __device__ __forceinline__ void st_release(uint64_t *p, uint64_t v)
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t *start, int64_t n,
-                                                       uint64_t *status, int32_t tiles, Control *ctl)
+                                                       uint64_t *status, int32_t tiles, ScanCtl *sc, Control *ctl)
 {
     __shared__ int32_t s_tile;
     __shared__ uint32_t s_epoch;
@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t
     __shared__ uint32_t s_prefix;
     kernel_enter(ctl, KID_SCAN);
     if (threadIdx.x == 0) {
-        s_tile = atomicAdd(&ctl->scan_tile_counter, 1);
-        s_epoch = *reinterpret_cast<volatile uint32_t *>(&ctl->scan_epoch);
+        s_tile = atomicAdd(&sc->tile_counter, 1);
+        s_epoch = *reinterpret_cast<volatile uint32_t *>(&sc->epoch);
     }
     __syncthreads();
     const int32_t tile = s_tile;
@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&ctl->scan_done, 1) == tiles - 1) {
-            ctl->scan_tile_counter = 0;
-            ctl->scan_done = 0;
+        if (atomicAdd(&sc->done, 1) == tiles - 1) {
+            sc->tile_counter = 0;
+            sc->done = 0;
             uint32_t e = (s_epoch + 1u) & 0x3fffffffu;
-            ctl->scan_epoch = e == 0 ? 1u : e;
+            sc->epoch = e == 0 ? 1u : e;
             __threadfence();
         }
     }
@@ -225,10 +225,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t
 int32_t scan_tiles_for(int64_t n) { return (int32_t)((n + kScanTile - 1) / kScanTile); }
 
 void launch_scan(uint32_t *count, uint32_t *start, int64_t n, uint64_t *status, int32_t tiles,
-                 Control *ctl, cudaStream_t s)
+                 ScanCtl *sc, Control *ctl, cudaStream_t s)
 {
     if (n <= 0 || tiles <= 0) return;
-    k_scan<<<tiles, kScanThreads, 0, s>>>(count, start, n, status, tiles, ctl);
+    k_scan<<<tiles, kScanThreads, 0, s>>>(count, start, n, status, tiles, sc, ctl);
 }
 
 void launch_key_hist(const Ptrs &P, SortWhat what, cudaStream_t s)
@@ -242,9 +242,12 @@ void launch_key_hist(const Ptrs &P, SortWhat what, cudaStream_t s)
 void launch_scan_cells(const Ptrs &P, SortWhat what, cudaStream_t s)
 {
     if (what == SORT_FLUID) {
-        if (P.nfblk) launch_scan(P.cell_count, P.cell_start, P.NC, P.scan_status, scan_tiles_for(P.NC), P.ctl, s);
+        if (P.nfblk)
+            launch_scan(P.cell_count, P.cell_start, P.NC, P.scan_status, scan_tiles_for(P.NC), &P.ctl->scan[0],
+                        P.ctl, s);
     } else if (P.nbblk) {
-        launch_scan(P.bcell_count, P.bcell_start, P.NC, P.scan_status, scan_tiles_for(P.NC), P.ctl, s);
+        launch_scan(P.bcell_count, P.bcell_start, P.NC, P.bscan_status, scan_tiles_for(P.NC), &P.ctl->scan[1],
+                    P.ctl, s);
     }
 }
 void launch_scatter(const Ptrs &P, SortWhat what, cudaStream_t s)

@@ -89,6 +89,15 @@ struct BodyDev {
     int32_t pad;
 };
 
+// State of one decoupled look-back scan: tile ticket, finished tiles, epoch of the tile
+// words (the fluid and the boundary sort each own one, so the two can run concurrently).
+struct ScanCtl {
+    int32_t tile_counter;
+    int32_t done;
+    uint32_t epoch;
+    int32_t pad;
+};
+
 // Context-wide control words (device).
 struct Control {
     uint32_t passb_counter;           // last-block counter of pass B (all scenes)
@@ -98,9 +107,7 @@ struct Control {
     int64_t launches;                 // kernel launches counted on the device
     float dt_override;                // > 0: fixed step for all scenes
     int32_t nscenes;
-    int32_t scan_tile_counter;        // decoupled look-back tile ticket
-    int32_t scan_done;
-    uint32_t scan_epoch;
+    ScanCtl scan[2];                  // look-back state of the fluid (0) and boundary (1) sorts
     int32_t error;                    // bounded-wait failures
     int32_t have_mlp;                 // warm-start network loaded
     uint32_t trace_n, trace_cap;      // device trace: stamps written / capacity
@@ -197,7 +204,8 @@ struct Ptrs {
     // reductions
     double *partial;                  // [ntblk]
     double *body_partial;             // [body][6][ntblk] per-block force/torque partials
-    uint64_t *scan_status;            // [tiles]
+    uint64_t *scan_status;            // [tiles] look-back words of the fluid sort
+    uint64_t *bscan_status;           // [tiles] and of the boundary sort
     int32_t scan_tiles;
     // implicit viscosity CG
     float4 *cg_r, *cg_p, *cg_ap;
@@ -234,7 +242,7 @@ void launch_scan_cells(const Ptrs &P, SortWhat what, cudaStream_t s);
 void launch_scatter(const Ptrs &P, SortWhat what, cudaStream_t s);
 void launch_rank_gather(const Ptrs &P, SortWhat what, cudaStream_t s);
 void launch_scan(uint32_t *count, uint32_t *start, int64_t n, uint64_t *status, int32_t tiles,
-                 Control *ctl, cudaStream_t s);
+                 ScanCtl *sc, Control *ctl, cudaStream_t s);
 int32_t scan_tiles_for(int64_t n);
 
 // ------------------------------------------------------------------ fluid (sph_fluid.cu)

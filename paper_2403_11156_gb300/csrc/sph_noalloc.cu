@@ -70,9 +70,9 @@ __global__ void k_na_clear(View v, int64_t ncell, int32_t tiles)
     for (int64_t c = k; c < ncell; c += stride) v.count[c] = 0u;
     for (int64_t t = k; t < tiles; t += stride) v.status[t] = 0ull;
     if (k == 0) {
-        v.ctl->scan_tile_counter = 0;
-        v.ctl->scan_done = 0;
-        v.ctl->scan_epoch = 0;
+        v.ctl->scan[0].tile_counter = 0;
+        v.ctl->scan[0].done = 0;
+        v.ctl->scan[0].epoch = 0;
         v.ctl->error = 0;
     }
 }
@@ -158,7 +158,7 @@ extern "C" sph_status sph_grid_order_noalloc(const float *x, int64_t n, const fl
     const int bp = (int)((n + t - 1) / t);
     k_na_clear<<<(int)std::min<int64_t>((ncell + t - 1) / t, 1184), t, 0, s>>>(v, ncell, tiles);
     k_na_key_hist<<<bp, t, 0, s>>>(v, g, x, n, keys);
-    launch_scan(v.count, v.start, ncell, v.status, tiles, v.ctl, s);
+    launch_scan(v.count, v.start, ncell, v.status, tiles, &v.ctl->scan[0], v.ctl, s);
     k_na_scatter<<<bp, t, 0, s>>>(v, n);
     k_na_rank<<<bp, t, 0, s>>>(v, n, order);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;

@@ -302,7 +302,7 @@ cudaError_t post_surface_field(const SceneDev &sc, const float4 *pos, const floa
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * ncell, s);
     if (e == cudaSuccess) {
         k_pf_hist<<<blocks_for(n), kPostBlock, 0, s>>>(pos, n, sc, count, key, slot);
-        launch_scan(count, start, ncell, status, scan_tiles_for(ncell), ctl, s);
+        launch_scan(count, start, ncell, status, scan_tiles_for(ncell), &ctl->scan[0], ctl, s);
         k_pf_place<<<blocks_for(n), kPostBlock, 0, s>>>(n, key, slot, start, cellidx);
         k_pf_rank<<<blocks_for(n), kPostBlock, 0, s>>>(pos, vel, n, sc.m, sc.rho0, key, start, cellidx, sorted);
         const int64_t nodes = (int64_t)dims[0] * dims[1] * dims[2];
@@ -356,7 +356,7 @@ extern "C" sph_status sph_surface_mesh(const float *field, const int32_t dims[3]
     uint32_t total = 0;
     if (e == cudaSuccess) {
         k_mt_count<<<blocks_for(cubes), kPostBlock, 0, s>>>(field, dims[0], dims[1], dims[2], iso, count);
-        launch_scan(count, start, cubes, status, scan_tiles_for(cubes), ctl, s);
+        launch_scan(count, start, cubes, status, scan_tiles_for(cubes), &ctl->scan[0], ctl, s);
         if (cap > 0)
             k_mt_emit<<<blocks_for(cubes), kPostBlock, 0, s>>>(field, dims[0], dims[1], dims[2], origin[0],
                                                                origin[1], origin[2], spacing, iso, start, tris, cap);
