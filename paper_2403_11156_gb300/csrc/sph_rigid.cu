@@ -101,14 +101,7 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     const SceneDev &sc = *c.sc;
     if (sc.nbody == 0 || (sc.strong != 0) != INC) return;  // uniform per block
     const int64_t i = c.i, NF = P.NF;
-    int nb = 0;
-    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-    float kt = 0.0f;
-    if (c.valid) {
-        nb = P.nnb[i];
-        pi = P.pos_s[i];
-        kt = INC ? pi.w : (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
-    }
+    const int nb = c.valid ? P.nnb[i] : 0;
     // which bodies this block's particles touch (most blocks touch none, or only walls):
     // untouched bodies get zero partials without a reduction
     __shared__ unsigned long long s_mask;
@@ -122,6 +115,14 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     if (mine) atomicOr(&s_mask, mine);
     __syncthreads();
     const unsigned long long touched = s_mask;
+    // the particle's own state is needed only in blocks that touch a body, and there only
+    // by particles with boundary neighbours
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    float kt = 0.0f;
+    if (touched && nb > 0) {
+        pi = P.pos_s[i];
+        kt = INC ? pi.w : (P.ksum[i] + P.kvsum[i]) / P.vel_c[i].w;
+    }
     for (int k = 0; k < sc.nbody; ++k) {
         double f[6] = {0, 0, 0, 0, 0, 0};
         const bool any = (touched >> k) & 1ull;
