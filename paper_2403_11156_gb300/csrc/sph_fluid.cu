@@ -2,16 +2,19 @@
 //
 // T threads (lanes, T = 1, 2 or 4) own one fluid particle in grid order.  The density
 // sweep walks the (2R+1)^3-cell neighbourhood ((2R+1)^2 contiguous index ranges) once
-// per step, lane s testing every T-th candidate of each range, and records each
-// neighbour's index in the lane's sub-list; every later sweep of the step (divergence
-// and density Jacobi passes, non-pressure forces, warm starts) gathers through those
-// sub-lists and combines the T partial sums with warp shuffles.  The solvers' error sums
-// are accumulated per block in FP64 and reduced in a fixed order by the last block of
-// each scene, which also decides the loop condition on the device (CUDA graph
-// conditional node).
-#include "sph_sweep.cuh"
-
+// per step and records the particle's neighbours in one k-major list, in candidate order
+// (with T > 1 the lanes test T consecutive candidates at a time and append the hits by a
+// ballot over the group, so the list is the same for every T).  Every later sweep of the
+// step (divergence and density Jacobi passes, non-pressure forces, warm starts) gathers
+// through that list, lane s taking entries s, s + T, ..., and combines the T partial sums
+// with warp shuffles.  The solvers' error sums are accumulated per block in FP64 and
+// reduced in a fixed order by the last block of each scene, which also decides the loop
+// condition on the device (CUDA graph conditional node).
 #include <math_constants.h>
+
+#include <type_traits>
+
+#include "sph_sweep.cuh"
 
 namespace sph {
 
@@ -179,14 +182,20 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
                 const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
                 if constexpr (T == 1) {
-                    for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
-                        float dx, dy2, dz2;
-                        const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-                        if (d2 < h2 && j != self) {
-                            if (nn_f < cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
-                            ++nn_f;
-                        }
-                    });
+                    // only the stencil's centre row holds the particle itself: the other
+                    // rows skip the self test
+                    auto scan = [&](auto check_self) {
+                        for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
+                            float dx, dy2, dz2;
+                            const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
+                            if (d2 < h2 && (!decltype(check_self)::value || j != self)) {
+                                if (nn_f < cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
+                                ++nn_f;
+                            }
+                        });
+                    };
+                    if (dz == 0 && dy == 0) scan(std::true_type{});
+                    else scan(std::false_type{});
                 } else {
                     for (uint32_t j0 = jb; j0 < je; j0 += (uint32_t)T) {   // uniform in the group
                         const uint32_t j = j0 + (uint32_t)s;
