@@ -257,6 +257,39 @@ def batched_throughput(steps=30, rank=0, world=1, barrier=lambda: None):
     return out
 
 
+def viscous_column_time(steps=300):
+    """The 250k-particle high-viscosity column (nu = 0.1 m^2/s, implicit viscosity by
+    matrix-free CG to 1e-4 relative residual every step) falling onto a plane: 300 graph
+    steps from rest; ms per step, CG and solver iterations per step."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    d = scenes.viscous_column()
+    n = len(d["fluid_x"])
+    stream = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cg = []
+    with sph.Context(d, stream=stream) as g:
+        g.sph_steps(3, 0.0)
+        g.sph_synchronize(raise_on_error=False)
+        s0 = g.sph_get_stats()
+        ms = 0.0
+        for _ in range(steps // 10):
+            a.record(stream)
+            g.sph_steps(10, 0.0)
+            b.record(stream)
+            st = g.sph_get_stats()              # synchronises
+            ms += a.elapsed_time(b)
+            cg.append(st["cg_iters"])
+        s1 = g.sph_get_stats()
+    k = (steps // 10) * 10
+    return {"fluid_particles": n, "boundary_particles": len(d["boundary_x"]), "steps": k,
+            "ms_per_step": ms / k, "particle_steps_per_s": n * k / (ms / 1000.0),
+            "cg_iters_last_step_mean": float(np.mean(cg)),
+            "density_iters_per_step": (s1["total_dens_iters"] - s0["total_dens_iters"]) / k,
+            "divergence_iters_per_step": (s1["total_div_iters"] - s0["total_div_iters"]) / k,
+            "dt": s1["dt"], "status_flags": s1["flags"]}
+
+
 def wcsph_step_time(steps=50):
     """The same 1.2M-particle dam break (without the boxes) under the WCSPH pressure solver
     (Sec. 3.4.1), the algorithm of the paper's only timing table (Table 1, whose particle
@@ -383,7 +416,9 @@ def main():
     ap.add_argument("--timing-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default 27-cell stencil and gather batch instead of autotuning")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batch measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the secondary workloads (64-scene batch, WCSPH, solver comparison, viscous column, "
+                         "post-processing)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-vs-plain warm-start comparison")
     args = ap.parse_args()
@@ -524,9 +559,11 @@ def main():
         batched = batched_throughput(rank=rank, world=world, barrier=barrier)
     wcsph = None
     solvers = None
+    column = None
     if rank == 0 and not args.no_batched:
         wcsph = wcsph_step_time()
         solvers = solver_comparison()
+        column = viscous_column_time()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -550,6 +587,7 @@ def main():
         "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
         "batched_64_scenes": batched,
         "wcsph_1.2M": wcsph,
+        "viscous_column_250k": column,
         "solvers_8k": solvers,
         "post_processing_1.2M": post,
     }
