@@ -290,6 +290,36 @@ def viscous_column_time(steps=300):
             "dt": s1["dt"], "status_flags": s1["flags"]}
 
 
+def coupling_comparison(steps=500):
+    """The 1.2M-particle rigid dam break with weak and with strong two-way coupling: 500
+    graph steps from rest (the boxes fall about 0.4 s before they sit in the flow); ms per
+    step, solver iterations per step and the boxes' final speeds."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    out = {}
+    for name, mode in (("weak", scenes.COUPLING_WEAK), ("strong", scenes.COUPLING_STRONG)):
+        d = scenes.dam_break_rigid(rigid_coupling=mode)
+        n = len(d["fluid_x"])
+        stream = torch.cuda.Stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with sph.Context(d, stream=stream) as g:
+            g.sph_steps(3, 0.0)
+            g.sph_synchronize(raise_on_error=False)
+            s0 = g.sph_get_stats()
+            a.record(stream)
+            g.sph_steps(steps, 0.0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            s1 = g.sph_get_stats()
+            bodies = g.sph_read_bodies()
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms / 1000.0),
+                     "density_iters_per_step": (s1["total_dens_iters"] - s0["total_dens_iters"]) / steps,
+                     "divergence_iters_per_step": (s1["total_div_iters"] - s0["total_div_iters"]) / steps,
+                     "box_speeds": [float(np.linalg.norm(bd[7:10])) for bd in bodies]}
+    return out
+
+
 def wcsph_step_time(steps=50):
     """The same 1.2M-particle dam break (without the boxes) under the WCSPH pressure solver
     (Sec. 3.4.1), the algorithm of the paper's only timing table (Table 1, whose particle
@@ -418,7 +448,7 @@ def main():
                     help="use the default 27-cell stencil and gather batch instead of autotuning")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the secondary workloads (64-scene batch, WCSPH, solver comparison, viscous column, "
-                         "post-processing)")
+                         "weak vs strong coupling, post-processing)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-vs-plain warm-start comparison")
     args = ap.parse_args()
@@ -560,10 +590,12 @@ def main():
     wcsph = None
     solvers = None
     column = None
+    coupling = None
     if rank == 0 and not args.no_batched:
         wcsph = wcsph_step_time()
         solvers = solver_comparison()
         column = viscous_column_time()
+        coupling = coupling_comparison()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -588,6 +620,7 @@ def main():
         "batched_64_scenes": batched,
         "wcsph_1.2M": wcsph,
         "viscous_column_250k": column,
+        "coupling_1.2M": coupling,
         "solvers_8k": solvers,
         "post_processing_1.2M": post,
     }
