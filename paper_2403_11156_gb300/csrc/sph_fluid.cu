@@ -234,12 +234,13 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
         // phase 2: density, alpha and the warm-start gate over the recorded list (this
         // lane's share of its entries)
         float w_sum = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f, div_f = 0.0f;
+        const Spline sp(sc);
         for_list<2, T, false>(nbr, NF, i, s, min(nn_f, cap_f), [&](int32_t j) {
             const float4 pj = __ldg(P.pos_s + j);
             float dx, dy2, dz2;
             const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-            w_sum += spline_w(sqrtf(d2) * sc.inv_h);
-            const float f = grad_factor(sc, d2);
+            w_sum += spline_w(sqrtf(d2) * sp.inv_h);
+            const float f = grad_factor(sp, d2);
             const float gx = f * dx, gy = f * dy2, gz = f * dz2;
             fx += gx; fy += gy; fz += gz;
             s2 = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, s2)));
@@ -261,8 +262,8 @@ __global__ void __launch_bounds__(kBlock) k_density_alpha(Ptrs P)
                 float dx, dy2, dz2;
                 const float d2 = pred_d2(pi, pb, dx, dy2, dz2);
                 const float psi = pb.w;
-                wb += psi * spline_w(sqrtf(d2) * sc.inv_h);
-                const float f = psi * grad_factor(sc, d2);
+                wb += psi * spline_w(sqrtf(d2) * sp.inv_h);
+                const float f = psi * grad_factor(sp, d2);
                 const float gx = f * dx, gy = f * dy2, gz = f * dz2;
                 s1x += gx; s1y += gy; s1z += gz;
                 if (gate) {
@@ -312,12 +313,13 @@ __device__ __forceinline__ float drho_dt_lane(const Ptrs &P, const SceneDev &sc,
                                               float4 vi, const float4 *__restrict__ V)
 {
     const int64_t NF = P.NF;
+    const Spline sp(sc);
     float acc = 0.0f;
     for_list<B, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
         const float4 pj = __ldg(P.pos_s + j);
         const float4 vj = __ldg(V + j);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float f = grad_factor(sp, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         acc = fmaf(f, (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz, acc);
     });
     float accb = 0.0f;
@@ -325,7 +327,7 @@ __device__ __forceinline__ float drho_dt_lane(const Ptrs &P, const SceneDev &sc,
     for_list<4, T>(P.bnbr, NF, i, s, P.nnb[i], [&](int32_t b) {
         const float4 pb = __ldg(P.bpos_s + b);
         const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
-        const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float f = pb.w * grad_factor(sp, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         float ux = vi.x, uy = vi.y, uz = vi.z;
         if (moving) {
             const float4 vb = __ldg(P.bvel_s + b);
@@ -436,10 +438,11 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
         if (c.valid) {
             const float4 pi = P.pos_s[i];
             const float ki = pi.w;
+            const Spline sp(sc);
             for_list<B, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
                 const float4 pj = __ldg(P.pos_s + j);
                 const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                const float f = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
+                const float f = grad_factor(sp, fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * (ki + pj.w);
                 ax = fmaf(f, dx, ax); ay = fmaf(f, dy, ay); az = fmaf(f, dz, az);
             });
             ax *= sc.m; ay *= sc.m; az *= sc.m;
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
                 for_list<4, T>(P.bnbr, NF, i, s, P.nnb[i], [&](int32_t b) {
                     const float4 pb = __ldg(P.bpos_s + b);
                     const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
-                    const float f = pb.w * grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    const float f = pb.w * grad_factor(sp, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     bx = fmaf(f, dx, bx); by = fmaf(f, dy, by); bz = fmaf(f, dz, bz);
                 });
                 ax = fmaf(ki, bx, ax); ay = fmaf(ki, by, ay); az = fmaf(ki, bz, az);
@@ -521,6 +524,7 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
             const float4 pi = P.pos_s[i];
             const float reg = 0.01f * sc.h2;
             const bool lap = sc.visc_mode == 1;
+            const Spline sp(sc);
             for_list<kBatch, T>(P.nbr, NF, i, s, P.nnf[i], [&](int32_t j) {
                 const float4 pj = __ldg(P.pos_s + j);
                 const float4 vj = __ldg(P.vel_s + j);
@@ -528,11 +532,11 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
                 const float ux = vi.x - vj.x, uy = vi.y - vj.y, uz = vi.z - vj.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (lap) {
-                    const float f = grad_factor(sc, r2);
+                    const float f = grad_factor(sp, r2);
                     const float q = f * (ux * dx + uy * dy + uz * dz) / ((r2 + reg) * vj.w);
                     sx = fmaf(q, dx, sx); sy = fmaf(q, dy, sy); sz = fmaf(q, dz, sz);
                 } else {
-                    const float w = spline_w(sqrtf(r2) * sc.inv_h) / vj.w;
+                    const float w = spline_w(sqrtf(r2) * sp.inv_h) / vj.w;
                     sx = fmaf(-w, ux, sx); sy = fmaf(-w, uy, sy); sz = fmaf(-w, uz, sz);
                 }
             });

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving
     const int32_t cz = cell_coord(pb.z, sc.origin[2], sc.cell, sc.dims[2]);
     const int32_t R = sc.R;
     const int32_t x0 = max(cx - R, 0), x1 = min(cx + R, sc.dims[0] - 1);
+    const float h2 = sc.h2, inv_h = sc.inv_h;
     float ws = 0.0f;
     for (int32_t dz = -R; dz <= R; ++dz) {
         const int32_t z = cz + dz;
@@ -65,8 +66,8 @@ __global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving
                 if ((int64_t)k == b) continue;
                 float dx, dy2, dz2;
                 const float d2 = pred_d2(pb, P.bpos_s[k], dx, dy2, dz2);
-                if (!(d2 < sc.h2)) continue;
-                ws += spline_w(sqrtf(d2) * sc.inv_h);
+                if (!(d2 < h2)) continue;
+                ws += spline_w(sqrtf(d2) * inv_h);
             }
         }
     }
@@ -128,12 +129,13 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
         const bool any = (touched >> k) & 1ull;
         if (any) {
             const BodyDev &B = P.bodies[sc.body_off + k];
+            const Spline sp(sc);
             for (int t = c.s; t < nb; t += T) {
                 const int32_t b = P.bnbr[(int64_t)t * NF + i];
                 if (P.bbody_s[b] != k) continue;
                 const float4 pb = P.bpos_s[b];
                 const float dx = pi.x - pb.x, dy = pi.y - pb.y, dz = pi.z - pb.z;
-                const float g = grad_factor(sc, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                const float g = grad_factor(sp, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                 const double s = (double)sc.m * (double)pb.w * (double)kt * (double)g;
                 const double Fx = s * dx, Fy = s * dy, Fz = s * dz;
                 const double rx = (double)pb.x - B.com[0], ry = (double)pb.y - B.com[1], rz = (double)pb.z - B.com[2];

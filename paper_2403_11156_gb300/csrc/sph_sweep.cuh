@@ -24,15 +24,23 @@ __device__ __forceinline__ float spline_w(float q)
     return 2.0f * t * t * t;
 }
 
+// The two constants of the spline gradient, copied into registers before a list walk (a
+// reference into the scene record would let the compiler reload them per pair).
+struct Spline {
+    float inv_h, kgrad;
+    __device__ __forceinline__ explicit Spline(const SceneDev &sc) : inv_h(sc.inv_h), kgrad(sc.kgrad) {}
+};
+
 // grad W_ij = factor * x_ij; zero for coincident particles.
-__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2)
+__device__ __forceinline__ float grad_factor(const Spline &k, float r2)
 {
     if (!(r2 > 0.0f)) return 0.0f;
     float rinv = rsqrtf(r2);
-    float q = r2 * rinv * sc.inv_h;
+    float q = r2 * rinv * k.inv_h;
     float g = (q <= 0.5f) ? q * fmaf(3.0f, q, -2.0f) : -(fmaxf(1.0f - q, 0.0f) * fmaxf(1.0f - q, 0.0f));
-    return sc.kgrad * g * rinv;
+    return k.kgrad * g * rinv;
 }
+__device__ __forceinline__ float grad_factor(const SceneDev &sc, float r2) { return grad_factor(Spline(sc), r2); }
 
 template <int T>
 struct Lane {

@@ -41,6 +41,7 @@ __device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, con
 {
     const int64_t NF = P.NF, i = c.i;
     const float reg = 0.01f * sc.h2;
+    const Spline sp(sc);
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
     if (c.valid) {
         for_list<4, T>(P.nbr, NF, i, c.s, P.nnf[i], [&](int32_t j) {
@@ -49,7 +50,7 @@ __device__ __forceinline__ float3 apply_m(const Ptrs &P, const SceneDev &sc, con
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             // grad W_ij (x_ij . (x_j - x_i)) / (rho_j (r^2 + reg))
-            const float q = grad_factor(sc, r2) * (dx * (xj.x - xi.x) + dy * (xj.y - xi.y) + dz * (xj.z - xi.z)) /
+            const float q = grad_factor(sp, r2) * (dx * (xj.x - xi.x) + dy * (xj.y - xi.y) + dz * (xj.z - xi.z)) /
                             (xj.w * (r2 + reg));
             ax = fmaf(q, dx, ax); ay = fmaf(q, dy, ay); az = fmaf(q, dz, az);
         });
