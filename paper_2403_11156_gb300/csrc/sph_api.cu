@@ -750,6 +750,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, P.bkey_tmp, NBa) && dalloc(c, P.bslot_tmp, NBa) && dalloc(c, P.bsid_tmp, NBa) &&
           dalloc(c, P.bsrc_tmp, NBa) && dalloc(c, P.bcell_tmp, NBa);
     ok &= dalloc(c, P.partial, std::max(ntblk, 1));
+    ok &= dalloc(c, P.partial2, std::max(ntblk, 1));
     ok &= dalloc(c, P.body_partial, (size_t)std::max(ntblk, 1) * std::max(nbodies, 1) * 6);
     if (c->any_implicit) {
         ok &= dalloc(c, P.cg_r, NF) && dalloc(c, P.cg_p, NF) && dalloc(c, P.cg_ap, NF);

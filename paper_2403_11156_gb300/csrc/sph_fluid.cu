@@ -67,6 +67,10 @@ __device__ __forceinline__ int warp_max(int v)
 }
 
 // Fixed-order block sum of one double per thread (deterministic).
+// Pass A's error partials are folded kFold at a time by pass B's blocks before its last
+// block sums the folds.
+constexpr int kFold = 8;
+
 __device__ double block_sum(double v, double *sh)
 {
     v = warp_sum(v);
@@ -98,7 +102,6 @@ __global__ void k_step_begin(Ptrs P)
     st.dt = od > 0.0f ? od : (sc.cfl > 0.0f ? st.dt_next : sc.dt_max);
     for (int k = 0; k < 2; ++k) {
         st.it[k] = 0;
-        st.pending[k] = 0;
         st.err[k] = CUDART_INF;
         st.err0[k] = 0.0;
     }
@@ -345,7 +348,6 @@ template <int S, int B, int T>
 __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 {
     __shared__ double sh[kBlock / 32];
-    __shared__ int s_last;
     kernel_enter(P.ctl, (KID_PASS_A0 + S));
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
@@ -387,32 +389,10 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
         set_w(P.pos_s, i, kappa / rho);
         e = (double)ei;
     }
-    double bsum = block_sum(e, sh);
-    if (threadIdx.x == 0) {
-        P.partial[blockIdx.x] = bsum;
-        __threadfence();
-        uint32_t prev = atomicAdd(&st.counter, 1u);
-        s_last = (prev == (uint32_t)sc.tblk_count - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    // last block of this scene: fixed-order sum of the scene's partials (L2 loads, several
-    // in flight per thread)
-    __threadfence();
-    double t = 0.0;
-    const double *part = P.partial + sc.tblk_first;
-    const int cnt = sc.tblk_count;
-#pragma unroll 8
-    for (int k = threadIdx.x; k < cnt; k += kBlock) t += __ldcg(part + k);
-    double total = block_sum(t, sh);
-    if (threadIdx.x == 0) {
-        double err = sc.nf > 0 ? total / (double)sc.nf / (double)sc.rho0 : 0.0;
-        if (S == 0) err *= (double)dt;
-        if (st.it[S] == 0) st.err0[S] = err;
-        st.err[S] = err;
-        st.pending[S] = 1;
-        st.counter = 0;
-    }
+    // the block's FP64 error partial; the pass B that follows reduces the partials in a
+    // fixed order (no last-block step here: pass A only has to finish)
+    const double bsum = block_sum(e, sh);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = bsum;
 }
 
 // Pass B (Alg. ppe_solver "update v*"): pressure acceleration of Sec. 3.3 Eq.
@@ -423,14 +403,17 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 template <int S, int WARM, int B, int T>
 __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
 {
-    __shared__ int s_last;
+    __shared__ int s_last, s_any;
+    __shared__ double sh[kBlock / 32];
     kernel_enter(P.ctl, (WARM ? KID_PASS_B0W + S : KID_PASS_B0 + S));
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
-    // uniform per block; WCSPH scenes apply their equation-of-state pressure here
+    // uniform per block; WCSPH scenes apply their equation-of-state pressure here.  In the
+    // loop, a scene's pass B runs exactly when its pass A did: the solver state only
+    // changes in the last block of this kernel.
     const bool run = WARM ? ((sc.warm != 0 && (S == 1 || sc.div_on)) || (S == 1 && sc.solver == 1))
-                          : (st.pending[S] != 0);
+                          : solver_active(sc, st, S);
     if (run) {
         const int64_t i = c.i, NF = P.NF;
         const int s = c.s;
@@ -467,28 +450,53 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
         }
     }
     if (WARM) return;
+    // fold pass A's error partials: the scene's first ceil(count / kFold) blocks each sum
+    // kFold consecutive ones in block order
+    if (run && threadIdx.x == 0) {
+        const int32_t lb = (int32_t)blockIdx.x - sc.tblk_first;
+        if (lb < (sc.tblk_count + kFold - 1) / kFold) {
+            const int32_t k0 = lb * kFold, k1 = min(k0 + kFold, sc.tblk_count);
+            double t = 0.0;
+            for (int32_t k = k0; k < k1; ++k) t += __ldcg(P.partial + sc.tblk_first + k);
+            P.partial2[blockIdx.x] = t;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         uint32_t prev = atomicAdd(&P.ctl->passb_counter, 1u);
         s_last = (prev == gridDim.x - 1u);
+        s_any = 0;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    // last block of the whole launch: advance the iteration counters, decide the loop
+    if (!s_last) return;
+    // last block of the whole launch: per scene whose solver ran, the fixed-order sum of the
+    // folds gives the mean error (Alg. ppe_solver's convergence test); then the iteration
+    // counters advance and the loop condition is set
     __threadfence();
-    uint32_t any = 0;
     for (int q = 0; q < P.nscenes; ++q) {
         const SceneDev &qd = P.scenes[q];
         SceneState &qs = P.st[q];
-        if (qs.pending[S]) {
-            qs.it[S] += 1;
-            qs.total_it[S] += 1;
-            qs.pending[S] = 0;
-            if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
+        if (solver_active(qd, qs, S)) {   // the same in every thread: nothing wrote qs yet
+            const int32_t nfold = (qd.tblk_count + kFold - 1) / kFold;
+            double t = 0.0;
+            for (int k = threadIdx.x; k < nfold; k += kBlock) t += __ldcg(P.partial2 + qd.tblk_first + k);
+            const double total = block_sum(t, sh);
+            if (threadIdx.x == 0) {
+                double err = qd.nf > 0 ? total / (double)qd.nf / (double)qd.rho0 : 0.0;
+                if (S == 0) err *= (double)qs.dt;
+                if (qs.it[S] == 0) qs.err0[S] = err;
+                qs.err[S] = err;
+                qs.it[S] += 1;
+                qs.total_it[S] += 1;
+                if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
+                if (solver_active(qd, qs, S)) s_any = 1;
+            }
         }
-        if (solver_active(qd, qs, S)) any = 1;
+        __syncthreads();
     }
+    if (threadIdx.x != 0) return;
+    uint32_t any = s_any;
     uint32_t guard = ++P.ctl->loop_guard;
     if (guard > 100000u) {
         any = 0;

@@ -65,9 +65,8 @@ struct SceneState {
     float maxv2;                      // written via atomicMax on the bit pattern
     int32_t flags;
     int32_t it[2];                    // iterations of the current step
-    int32_t pending[2];               // pass A ran in this loop iteration
     double err[2], err0[2];
-    uint32_t counter;                 // last-block counter of pass A
+    uint32_t counter;                 // last-block counter of the CG reductions
     int32_t max_nn_f, max_nn_b;
     int32_t cg_it;
     float cg_res;
@@ -202,7 +201,8 @@ struct Ptrs {
     uint32_t *bcell_count, *bcell_start;
     uint32_t *bkey_tmp, *bslot_tmp, *bsid_tmp, *bsrc_tmp, *bcell_tmp;
     // reductions
-    double *partial;                  // [ntblk]
+    double *partial;                  // [ntblk] pass A's FP64 error partial per block
+    double *partial2;                 // [ntblk] pass B's folds of kFold partials
     double *body_partial;             // [body][6][ntblk] per-block force/torque partials
     uint64_t *scan_status;            // [tiles] look-back words of the fluid sort
     uint64_t *bscan_status;           // [tiles] and of the boundary sort
