@@ -484,17 +484,19 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     auto loop = [&](int solver) -> sph_status {
         const char *na = solver == 0 ? "div_pass_a" : "dens_pass_a";
         const char *nb = solver == 0 ? "div_pass_b" : "dens_pass_b";
+        const char *nc = solver == 0 ? "div_check" : "dens_check";
         return device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
             run(c, q, na, [&] { launch_pass_a(P, solver, c->batch, q); });
-            run(c, q, nb, [&] { launch_pass_b(P, solver, 0, c->batch, h, use, q); });
+            run(c, q, nb, [&] { launch_pass_b(P, solver, 0, c->batch, q); });
             if (c->any_strong) run(c, q, "strong_coupling", [&] { launch_strong_update(P, q); });
+            run(c, q, nc, [&] { launch_solver_check(P, solver, h, use, q); });
         });
     };
 
     sph_status st;
     if (c->any_div) {
         if (c->any_warm_div) {
-            run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, 0, 0, s); });
+            run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, s); });
             if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
         }
         if ((st = loop(0)) != SPH_OK) return st;
@@ -516,7 +518,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     // the warm-start pressure of the density solve, or the WCSPH equation-of-state pressure
     // (written by the non-pressure kernel), applied once
     if (c->any_warm || c->any_wcsph) {
-        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, 0, 0, s); });
+        run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, s); });
         if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
     }
     if ((st = loop(1)) != SPH_OK) return st;

@@ -401,17 +401,15 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 //   v_i -= dt [ sum_j m (k_i/rho_i + k_j/rho_j) grad W_ij + sum_b Psi_b (k_i/rho_i) grad W_ib ]
 // WARM = 1 applies the warm-start kappas (no loop bookkeeping).
 template <int S, int WARM, int B, int T>
-__global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
+__global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P)
 {
-    __shared__ int s_last, s_any;
-    __shared__ double sh[kBlock / 32];
     kernel_enter(P.ctl, (WARM ? KID_PASS_B0W + S : KID_PASS_B0 + S));
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     SceneState &st = *c.st;
     // uniform per block; WCSPH scenes apply their equation-of-state pressure here.  In the
     // loop, a scene's pass B runs exactly when its pass A did: the solver state only
-    // changes in the last block of this kernel.
+    // changes in the check kernel that follows.
     const bool run = WARM ? ((sc.warm != 0 && (S == 1 || sc.div_on)) || (S == 1 && sc.solver == 1))
                           : solver_active(sc, st, S);
     if (run) {
@@ -451,7 +449,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
     }
     if (WARM) return;
     // fold pass A's error partials: the scene's first ceil(count / kFold) blocks each sum
-    // kFold consecutive ones in block order
+    // kFold consecutive ones in block order (the check kernel, a later launch, sums the folds)
     if (run && threadIdx.x == 0) {
         const int32_t lb = (int32_t)blockIdx.x - sc.tblk_first;
         if (lb < (sc.tblk_count + kFold - 1) / kFold) {
@@ -461,40 +459,71 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
             P.partial2[blockIdx.x] = t;
         }
     }
+}
+
+// Convergence test of one Jacobi iteration (Alg. ppe_solver's loop condition), one block
+// of 1024 threads after pass B.  A scene's folds are summed in a fixed order: with a few
+// scenes the whole block takes each in turn (thread t sums folds t, t + 1024, ..., then a
+// fixed tree), with many one warp per scene (lane l sums folds l, l + 32, ..., then a
+// butterfly).  The sum gives the mean error; the iteration counters advance and the loop
+// condition is set for the host and for the CUDA graph's while node.
+__device__ __forceinline__ void finish_iteration(const SceneDev &qd, SceneState &qs, int S, double total, int *s_any)
+{
+    double err = qd.nf > 0 ? total / (double)qd.nf / (double)qd.rho0 : 0.0;
+    if (S == 0) err *= (double)qs.dt;
+    if (qs.it[S] == 0) qs.err0[S] = err;
+    qs.err[S] = err;
+    qs.it[S] += 1;
+    qs.total_it[S] += 1;
+    if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
+    if (solver_active(qd, qs, S)) atomicOr(s_any, 1);
+}
+
+constexpr int kCheckThreads = 1024;
+constexpr int kCheckBlockWideScenes = 4;   // up to this many scenes: block-wide sums
+
+template <int S>
+__global__ void __launch_bounds__(kCheckThreads) k_solver_check(Ptrs P, cudaGraphConditionalHandle handle,
+                                                               int use_handle)
+{
+    __shared__ int s_any;
+    __shared__ double sh[kCheckThreads / 32];
+    kernel_enter(P.ctl, KID_CHECK0 + S);
+    if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        uint32_t prev = atomicAdd(&P.ctl->passb_counter, 1u);
-        s_last = (prev == gridDim.x - 1u);
-        s_any = 0;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    // last block of the whole launch: per scene whose solver ran, the fixed-order sum of the
-    // folds gives the mean error (Alg. ppe_solver's convergence test); then the iteration
-    // counters advance and the loop condition is set
-    __threadfence();
-    for (int q = 0; q < P.nscenes; ++q) {
-        const SceneDev &qd = P.scenes[q];
-        SceneState &qs = P.st[q];
-        if (solver_active(qd, qs, S)) {   // the same in every thread: nothing wrote qs yet
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (P.nscenes <= kCheckBlockWideScenes) {
+        for (int q = 0; q < P.nscenes; ++q) {
+            const SceneDev &qd = P.scenes[q];
+            SceneState &qs = P.st[q];
+            if (!solver_active(qd, qs, S)) continue;   // uniform: nothing wrote qs yet
             const int32_t nfold = (qd.tblk_count + kFold - 1) / kFold;
             double t = 0.0;
-            for (int k = threadIdx.x; k < nfold; k += kBlock) t += __ldcg(P.partial2 + qd.tblk_first + k);
-            const double total = block_sum(t, sh);
-            if (threadIdx.x == 0) {
-                double err = qd.nf > 0 ? total / (double)qd.nf / (double)qd.rho0 : 0.0;
-                if (S == 0) err *= (double)qs.dt;
-                if (qs.it[S] == 0) qs.err0[S] = err;
-                qs.err[S] = err;
-                qs.it[S] += 1;
-                qs.total_it[S] += 1;
-                if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
-                if (solver_active(qd, qs, S)) s_any = 1;
+            for (int k = threadIdx.x; k < nfold; k += kCheckThreads) t += __ldcg(P.partial2 + qd.tblk_first + k);
+            t = warp_sum(t);
+            if (lane == 0) sh[warp] = t;
+            __syncthreads();
+            if (warp == 0) {
+                double u = sh[lane];
+                u = warp_sum(u);
+                if (lane == 0) finish_iteration(qd, qs, S, u, &s_any);
             }
+            __syncthreads();
         }
-        __syncthreads();
+    } else {
+        for (int q = warp; q < P.nscenes; q += kCheckThreads / 32) {
+            const SceneDev &qd = P.scenes[q];
+            SceneState &qs = P.st[q];
+            if (!solver_active(qd, qs, S)) continue;   // its pass A and B did not run
+            const int32_t nfold = (qd.tblk_count + kFold - 1) / kFold;
+            double t = 0.0;
+#pragma unroll 4
+            for (int k = lane; k < nfold; k += 32) t += __ldcg(P.partial2 + qd.tblk_first + k);
+            t = warp_sum(t);
+            if (lane == 0) finish_iteration(qd, qs, S, t, &s_any);
+        }
     }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     uint32_t any = s_any;
     uint32_t guard = ++P.ctl->loop_guard;
@@ -504,8 +533,6 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P, cudaGraphConditionalH
     }
     if (!any) P.ctl->loop_guard = 0;
     P.ctl->loop_flag = any;
-    P.ctl->passb_counter = 0;
-    __threadfence();
     if (use_handle) cudaGraphSetConditional(handle, any);
 }
 
@@ -775,10 +802,9 @@ void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s)
     else { if (solver == 0) SPH_A(0, 4, 1); else SPH_A(1, 4, 1); }
 #undef SPH_A
 }
-void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphConditionalHandle h, int use_handle,
-                   cudaStream_t s)
+void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaStream_t s)
 {
-#define SPH_B(S, W, B, T) k_pass_b<S, W, B, T><<<P.ntblk, kBlock, 0, s>>>(P, h, use_handle)
+#define SPH_B(S, W, B, T) k_pass_b<S, W, B, T><<<P.ntblk, kBlock, 0, s>>>(P)
 #define SPH_BW(B, T)                                                 \
     do {                                                             \
         if (solver == 0) { if (warm) SPH_B(0, 1, B, T); else SPH_B(0, 0, B, T); } \
@@ -790,6 +816,11 @@ void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphCond
     else SPH_BW(4, 1);
 #undef SPH_BW
 #undef SPH_B
+}
+void launch_solver_check(const Ptrs &P, int solver, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
+{
+    if (solver == 0) k_solver_check<0><<<1, kCheckThreads, 0, s>>>(P, h, use_handle);
+    else k_solver_check<1><<<1, kCheckThreads, 0, s>>>(P, h, use_handle);
 }
 void launch_nonpressure(const Ptrs &P, cudaStream_t s)
 {

@@ -148,7 +148,9 @@ enum KernelId : uint32_t {
     KID_MLP_WARM = 29,
     KID_BFORCE_INC = 30,
     KID_BAPPLY = 31,
-    KID_BVEL = 32
+    KID_BVEL = 32,
+    KID_CHECK0 = 33,
+    KID_CHECK1 = 34
 };
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
@@ -249,8 +251,8 @@ int32_t scan_tiles_for(int64_t n);
 void launch_step_begin(const Ptrs &P, cudaStream_t s);
 void launch_density_alpha(const Ptrs &P, cudaStream_t s);
 void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s);
-void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaGraphConditionalHandle h,
-                   int use_handle, cudaStream_t s);
+void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaStream_t s);
+void launch_solver_check(const Ptrs &P, int solver, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
 void launch_nonpressure(const Ptrs &P, cudaStream_t s);
 void launch_warm_density(const Ptrs &P, cudaStream_t s);
 void launch_advect(const Ptrs &P, cudaStream_t s);
