@@ -506,8 +506,10 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         run(c, s, "cg_init", [&] { launch_cg_init(P, s); });
         st = device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
             run(c, q, "cg_ap", [&] { launch_cg_ap(P, q); });
+            run(c, q, "cg_alpha", [&] { launch_cg_alpha(P, q); });
             run(c, q, "cg_xr", [&] { launch_cg_xr(P, q); });
-            run(c, q, "cg_p", [&] { launch_cg_p(P, h, use, q); });
+            run(c, q, "cg_beta", [&] { launch_cg_beta(P, h, use, q); });
+            run(c, q, "cg_p", [&] { launch_cg_p(P, q); });
         });
         if (st != SPH_OK) return st;
     }

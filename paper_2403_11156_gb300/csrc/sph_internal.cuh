@@ -150,7 +150,9 @@ enum KernelId : uint32_t {
     KID_BAPPLY = 31,
     KID_BVEL = 32,
     KID_CHECK0 = 33,
-    KID_CHECK1 = 34
+    KID_CHECK1 = 34,
+    KID_CG_ALPHA = 35,
+    KID_CG_BETA = 36
 };
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
@@ -266,8 +268,10 @@ cudaError_t mlp_prepare_kernels();
 // ------------------------------------------------------------------ implicit viscosity (sph_visc.cu)
 void launch_cg_init(const Ptrs &P, cudaStream_t s);
 void launch_cg_ap(const Ptrs &P, cudaStream_t s);
+void launch_cg_alpha(const Ptrs &P, cudaStream_t s);
 void launch_cg_xr(const Ptrs &P, cudaStream_t s);
-void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+void launch_cg_beta(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+void launch_cg_p(const Ptrs &P, cudaStream_t s);
 
 // ------------------------------------------------------------------ post-processing (sph_post.cu)
 cudaError_t post_surface_field(const SceneDev &sc, const float4 *pos, const float4 *vel, const float origin[3],

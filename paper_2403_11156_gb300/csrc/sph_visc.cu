@@ -7,7 +7,9 @@
 // on the fly from the neighbour lists; the CG vectors live in float4 arrays whose w lane
 // keeps rho so that one gather serves both.  Dot products are accumulated per block in
 // FP64 and reduced in a fixed order by the last block of each scene; the loop runs on the
-// device (CUDA graph while node) until |r| <= tol |b| or cg_max_iter.
+// device (CUDA graph while node) until |r| <= tol |b| or cg_max_iter.  Within an iteration
+// the two dot products are reduced by one-block kernels (alpha after the matrix sweep,
+// beta and the stopping test after the update), so the wide kernels only write partials.
 #include "sph_sweep.cuh"
 
 namespace sph {
@@ -128,6 +130,73 @@ __device__ __forceinline__ bool cg_active(const SceneDev &sc, const SceneState &
     return sc.visc_mode == 3 && st.cg_active != 0;
 }
 
+// Per-block partial sums of two doubles, written for a later one-block reduction.
+__device__ __forceinline__ void block_partials2(const Ptrs &P, double a, double b, double *sh)
+{
+    block_sum2(a, b, sh);
+    if (threadIdx.x == 0) {
+        P.cg_dots[2 * blockIdx.x] = a;
+        P.cg_dots[2 * blockIdx.x + 1] = b;
+    }
+}
+
+constexpr int kReduceThreads = 1024;
+
+// One block (kReduceThreads threads) sums, per scene with an active CG, the block partials
+// of the preceding launch over the scene's sweep blocks (SWEEP) or fluid blocks, in a fixed
+// order: with a few scenes the whole block takes each in turn, with many one warp per
+// scene.  done(scene, a, b) runs in one thread per scene.
+template <bool SWEEP, typename F>
+__device__ void reduce_scenes(const Ptrs &P, double *sh, F &&done)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double2 *d = reinterpret_cast<const double2 *>(P.cg_dots);
+    if (P.nscenes <= 4) {
+        for (int q = 0; q < P.nscenes; ++q) {
+            const SceneDev &qd = P.scenes[q];
+            if (!cg_active(qd, P.st[q])) continue;   // uniform: nothing wrote the state yet
+            const int32_t first = SWEEP ? qd.tblk_first : qd.fblk_first;
+            const int32_t count = SWEEP ? qd.tblk_count : qd.fblk_count;
+            double a = 0.0, b = 0.0;
+            for (int k = threadIdx.x; k < count; k += kReduceThreads) {
+                const double2 v = __ldcg(d + first + k);
+                a += v.x;
+                b += v.y;
+            }
+            a = warp_sum(a);
+            b = warp_sum(b);
+            if (lane == 0) {
+                sh[2 * warp] = a;
+                sh[2 * warp + 1] = b;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double u = sh[2 * lane], w = sh[2 * lane + 1];
+                u = warp_sum(u);
+                w = warp_sum(w);
+                if (lane == 0) done(q, u, w);
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int q = warp; q < P.nscenes; q += kReduceThreads / 32) {
+            const SceneDev &qd = P.scenes[q];
+            if (!cg_active(qd, P.st[q])) continue;
+            const int32_t first = SWEEP ? qd.tblk_first : qd.fblk_first;
+            const int32_t count = SWEEP ? qd.tblk_count : qd.fblk_count;
+            double a = 0.0, b = 0.0;
+            for (int k = lane; k < count; k += 32) {
+                const double2 v = __ldcg(d + first + k);
+                a += v.x;
+                b += v.y;
+            }
+            a = warp_sum(a);
+            b = warp_sum(b);
+            if (lane == 0) done(q, a, b);
+        }
+    }
+}
+
 // x0 = v~ (already in vel_c), r0 = b - (I - dt A) x0, p0 = r0; |r0|^2 and |b|^2.
 template <int T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
@@ -161,12 +230,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(Ptrs P)
     }
 }
 
-// Ap = (I - dt A) p; alpha = |r|^2 / p.Ap.
+// Ap = (I - dt A) p and the block partials of p.Ap.
 template <int T>
 __global__ void __launch_bounds__(kBlock) k_cg_ap(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
-    __shared__ int s_last;
     kernel_enter(P.ctl, KID_CG_AP);
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
@@ -181,15 +249,24 @@ __global__ void __launch_bounds__(kBlock) k_cg_ap(Ptrs P)
         P.cg_ap[i] = make_float4(ap.x, ap.y, ap.z, 0.0f);
         pap = (double)p.x * ap.x + (double)p.y * ap.y + (double)p.z * ap.z;
     }
-    if (scene_reduce2(P, sc.tblk_first, sc.tblk_count, st, pap, unused, sh, &s_last))
-        st.cg_alpha = pap > 0.0 ? st.cg_rr / pap : 0.0;
+    block_partials2(P, pap, unused, sh);
 }
 
-// x += alpha p, r -= alpha Ap; beta = |r_new|^2 / |r|^2.
+// alpha = |r|^2 / p.Ap per scene (one block).
+__global__ void __launch_bounds__(kReduceThreads) k_cg_alpha(Ptrs P)
+{
+    __shared__ double sh[2 * kReduceThreads / 32];
+    kernel_enter(P.ctl, KID_CG_ALPHA);
+    reduce_scenes<true>(P, sh, [&](int q, double pap, double) {
+        SceneState &qs = P.st[q];
+        qs.cg_alpha = pap > 0.0 ? qs.cg_rr / pap : 0.0;
+    });
+}
+
+// x += alpha p, r -= alpha Ap and the block partials of |r_new|^2.
 __global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
 {
     __shared__ double sh[2 * kBlock / 32];
-    __shared__ int s_last;
     kernel_enter(P.ctl, KID_CG_XR);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
@@ -209,18 +286,47 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Ptrs P)
         P.cg_r[i] = r;
         rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
     }
-    if (scene_reduce2(P, sc.fblk_first, sc.fblk_count, st, rr, unused, sh, &s_last)) {
-        st.cg_beta = st.cg_rr > 0.0 ? rr / st.cg_rr : 0.0;
-        st.cg_rr = rr;
-        st.cg_it += 1;
-        st.cg_res = st.cg_bb > 0.0 ? (float)sqrt(rr / st.cg_bb) : 0.0f;
-    }
+    block_partials2(P, rr, unused, sh);
 }
 
-// p = r + beta p; the last block of the launch decides whether any scene continues.
-__global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P, cudaGraphConditionalHandle handle, int use_handle)
+// beta = |r_new|^2 / |r|^2 per scene, the iteration count and the residual; a scene stops
+// at |r| <= tol |b| or cg_max_iter, and the loop goes on while any scene continues (one
+// block; sets the CUDA graph's while condition).
+__global__ void __launch_bounds__(kReduceThreads) k_cg_beta(Ptrs P, cudaGraphConditionalHandle handle,
+                                                           int use_handle)
 {
-    __shared__ int s_last;
+    __shared__ double sh[2 * kReduceThreads / 32];
+    __shared__ int s_any;
+    kernel_enter(P.ctl, KID_CG_BETA);
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    reduce_scenes<false>(P, sh, [&](int q, double rr, double) {
+        const SceneDev &qd = P.scenes[q];
+        SceneState &qs = P.st[q];
+        qs.cg_beta = qs.cg_rr > 0.0 ? rr / qs.cg_rr : 0.0;
+        qs.cg_rr = rr;
+        qs.cg_it += 1;
+        qs.cg_res = qs.cg_bb > 0.0 ? (float)sqrt(rr / qs.cg_bb) : 0.0f;
+        const double tol = (double)qd.cg_tol;
+        if (qs.cg_it >= qd.cg_max || !(qs.cg_rr > tol * tol * qs.cg_bb)) qs.cg_active = 0;
+        else atomicOr(&s_any, 1);
+    });
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    uint32_t any = s_any;
+    uint32_t guard = ++P.ctl->loop_guard;
+    if (guard > 100000u) {
+        any = 0;
+        P.ctl->error = 3;
+    }
+    if (!any) P.ctl->loop_guard = 0;
+    P.ctl->loop_flag = any;
+    if (use_handle) cudaGraphSetConditional(handle, any);
+}
+
+// p = r + beta p for the scenes whose CG goes on.
+__global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P)
+{
     kernel_enter(P.ctl, KID_CG_P);
     Ctx c = ctx(P);
     const SceneDev &sc = *c.sc;
@@ -233,34 +339,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(Ptrs P, cudaGraphConditionalHan
         p.x = fmaf(b, p.x, r.x); p.y = fmaf(b, p.y, r.y); p.z = fmaf(b, p.z, r.z);
         P.cg_p[i] = p;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        uint32_t prev = atomicAdd(&P.ctl->passb_counter, 1u);
-        s_last = (prev == gridDim.x - 1u);
-    }
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    uint32_t any = 0;
-    for (int s = 0; s < P.nscenes; ++s) {
-        const SceneDev &q = P.scenes[s];
-        SceneState &qs = P.st[s];
-        if (q.visc_mode != 3 || !qs.cg_active) continue;
-        const double tol = (double)q.cg_tol;
-        if (qs.cg_it >= q.cg_max || !(qs.cg_rr > tol * tol * qs.cg_bb)) qs.cg_active = 0;
-        else any = 1;
-    }
-    uint32_t guard = ++P.ctl->loop_guard;
-    if (guard > 100000u) {
-        any = 0;
-        P.ctl->error = 3;
-    }
-    if (!any) P.ctl->loop_guard = 0;
-    P.ctl->loop_flag = any;
-    P.ctl->passb_counter = 0;
-    __threadfence();
-    if (use_handle) cudaGraphSetConditional(handle, any);
 }
 
 }  // namespace
@@ -277,10 +355,12 @@ void launch_cg_ap(const Ptrs &P, cudaStream_t s)
     SPH_BY_LANES(P, SPH_L);
 #undef SPH_L
 }
+void launch_cg_alpha(const Ptrs &P, cudaStream_t s) { k_cg_alpha<<<1, kReduceThreads, 0, s>>>(P); }
 void launch_cg_xr(const Ptrs &P, cudaStream_t s) { k_cg_xr<<<P.nfblk, kBlock, 0, s>>>(P); }
-void launch_cg_p(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
+void launch_cg_beta(const Ptrs &P, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
 {
-    k_cg_p<<<P.nfblk, kBlock, 0, s>>>(P, h, use_handle);
+    k_cg_beta<<<1, kReduceThreads, 0, s>>>(P, h, use_handle);
 }
+void launch_cg_p(const Ptrs &P, cudaStream_t s) { k_cg_p<<<P.nfblk, kBlock, 0, s>>>(P); }
 
 }  // namespace sph
