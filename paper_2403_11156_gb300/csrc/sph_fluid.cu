@@ -7,9 +7,10 @@
 // ballot over the group, so the list is the same for every T).  Every later sweep of the
 // step (divergence and density Jacobi passes, non-pressure forces, warm starts) gathers
 // through that list, lane s taking entries s, s + T, ..., and combines the T partial sums
-// with warp shuffles.  The solvers' error sums are accumulated per block in FP64 and
-// reduced in a fixed order by the last block of each scene, which also decides the loop
-// condition on the device (CUDA graph conditional node).
+// with warp shuffles.  The solvers' error sums are accumulated per block in FP64 by pass A,
+// folded eight at a time by pass B and summed in a fixed order by a one-block check
+// kernel, which also decides the loop condition on the device (CUDA graph conditional
+// node).
 #include <math_constants.h>
 
 #include <type_traits>
@@ -91,7 +92,6 @@ __global__ void k_step_begin(Ptrs P)
     kernel_enter(P.ctl, KID_STEP_BEGIN);
     int s = threadIdx.x + blockIdx.x * blockDim.x;
     if (s == 0) {
-        P.ctl->passb_counter = 0;
         P.ctl->loop_guard = 0;
         P.ctl->mlp_n = 0;
     }

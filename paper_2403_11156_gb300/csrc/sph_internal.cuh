@@ -66,7 +66,7 @@ struct SceneState {
     int32_t flags;
     int32_t it[2];                    // iterations of the current step
     double err[2], err0[2];
-    uint32_t counter;                 // last-block counter of the CG reductions
+    uint32_t counter;                 // last-block counter of the CG's initial residual
     int32_t max_nn_f, max_nn_b;
     int32_t cg_it;
     float cg_res;
@@ -99,7 +99,7 @@ struct ScanCtl {
 
 // Context-wide control words (device).
 struct Control {
-    uint32_t passb_counter;           // last-block counter of pass B (all scenes)
+    uint32_t pad_c;
     uint32_t loop_flag;               // host-readable copy of the loop condition
     uint32_t loop_guard;              // iterations of the current loop
     uint32_t pad0;

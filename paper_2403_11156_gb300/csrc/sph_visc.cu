@@ -6,10 +6,11 @@
 // d = 3, mbar = m (one particle mass per scene), mu = nu rho0.  The operator is applied
 // on the fly from the neighbour lists; the CG vectors live in float4 arrays whose w lane
 // keeps rho so that one gather serves both.  Dot products are accumulated per block in
-// FP64 and reduced in a fixed order by the last block of each scene; the loop runs on the
-// device (CUDA graph while node) until |r| <= tol |b| or cg_max_iter.  Within an iteration
-// the two dot products are reduced by one-block kernels (alpha after the matrix sweep,
-// beta and the stopping test after the update), so the wide kernels only write partials.
+// FP64 and summed per scene in a fixed order: the initial residual by the last block of
+// each scene, the two products of an iteration by one-block kernels (alpha after the
+// matrix sweep, beta and the stopping test after the update), so the wide kernels of the
+// loop only write partials.  The loop runs on the device (CUDA graph while node) until
+// |r| <= tol |b| or cg_max_iter.
 #include "sph_sweep.cuh"
 
 namespace sph {
