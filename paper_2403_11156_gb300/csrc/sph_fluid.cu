@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kBlock, 9) k_density_alpha(Ptrs P)
         };
         const int cap_f = sc.cap_f, cap_b = sc.cap_b;
         const uint32_t self = (uint32_t)i;
+        int32_t *slot_f = P.nbr + i;   // this particle's next list entry (one lane per particle)
         // the group's lanes relative to this one (cooperative append for T > 1)
         const unsigned gmask = group_mask<T>();
         const int gshift = (int)(threadIdx.x & 31u) & ~(T - 1);
@@ -189,14 +190,16 @@ __global__ void __launch_bounds__(kBlock, 9) k_density_alpha(Ptrs P)
                 if constexpr (T == 1) {
                     // only the stencil's centre row holds the particle itself: the other
                     // rows skip the self test
+                    // the append is branch-free: a predicated store through a running
+                    // slot pointer, so most candidates (rejected) cost no divergence
                     auto scan = [&](auto check_self) {
                         for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
                             float dx, dy2, dz2;
                             const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-                            if (d2 < h2 && (!decltype(check_self)::value || j != self)) {
-                                if (nn_f < cap_f) P.nbr[(int64_t)nn_f * NF + i] = (int32_t)j;
-                                ++nn_f;
-                            }
+                            const bool hit = d2 < h2 && (!decltype(check_self)::value || j != self);
+                            if (hit && nn_f < cap_f) *slot_f = (int32_t)j;
+                            slot_f += hit ? NF : 0;
+                            nn_f += hit;
                         });
                     };
                     if (dz == 0 && dy == 0) scan(std::true_type{});
