@@ -446,6 +446,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     run(c, s, "sort_rank_gather", [&] { launch_rank_gather(P, SORT_FLUID, s); });
     if (c->any_moving) CK(cudaStreamWaitEvent(s, c->join, 0));
     run(c, s, "density_alpha", [&] { launch_density_alpha(P, s); });
+    if (c->any_strong) run(c, s, "body_touch", [&] { launch_body_touch(P, s); });
 
     // A device-controlled loop: in capture mode a conditional while node whose body is
     // captured on the second stream; in eager mode the host reads the loop flag.
@@ -756,6 +757,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, P.partial, std::max(ntblk, 1));
     ok &= dalloc(c, P.partial2, std::max(ntblk, 1));
     ok &= dalloc(c, P.body_partial, (size_t)std::max(ntblk, 1) * std::max(nbodies, 1) * 6);
+    ok &= dalloc(c, P.blk_touch, std::max(ntblk, 1));
     if (c->any_implicit) {
         ok &= dalloc(c, P.cg_r, NF) && dalloc(c, P.cg_p, NF) && dalloc(c, P.cg_ap, NF);
         ok &= dalloc(c, P.cg_dots, 2 * (size_t)std::max(std::max(nfblk, ntblk), 1));

@@ -152,7 +152,8 @@ enum KernelId : uint32_t {
     KID_CHECK0 = 33,
     KID_CHECK1 = 34,
     KID_CG_ALPHA = 35,
-    KID_CG_BETA = 36
+    KID_CG_BETA = 36,
+    KID_BTOUCH = 37
 };
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
@@ -208,6 +209,7 @@ struct Ptrs {
     double *partial;                  // [ntblk] pass A's FP64 error partial per block
     double *partial2;                 // [ntblk] pass B's folds of kFold partials
     double *body_partial;             // [body][6][ntblk] per-block force/torque partials
+    unsigned long long *blk_touch;    // [ntblk] bodies each sweep block touches (strong coupling)
     uint64_t *scan_status;            // [tiles] look-back words of the fluid sort
     uint64_t *bscan_status;           // [tiles] and of the boundary sort
     int32_t scan_tiles;
@@ -284,6 +286,7 @@ void launch_boundary_update(const Ptrs &P, cudaStream_t s);
 void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);
 void launch_body_force(const Ptrs &P, cudaStream_t s);
 void launch_body_reduce(const Ptrs &P, cudaStream_t s);
+void launch_body_touch(const Ptrs &P, cudaStream_t s);
 void launch_strong_update(const Ptrs &P, cudaStream_t s);
 
 }  // namespace sph

@@ -103,19 +103,27 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
     if (sc.nbody == 0 || (sc.strong != 0) != INC) return;  // uniform per block
     const int64_t i = c.i, NF = P.NF;
     const int nb = c.valid ? P.nnb[i] : 0;
-    // which bodies this block's particles touch (most blocks touch none, or only walls):
-    // untouched bodies get zero partials without a reduction
-    __shared__ unsigned long long s_mask;
-    if (threadIdx.x == 0) s_mask = 0ull;
-    __syncthreads();
-    unsigned long long mine = 0ull;
-    for (int t = c.s; t < nb; t += T) {
-        const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * NF + i]];
-        if (k >= 0) mine |= 1ull << k;
+    // which bodies this block's particles touch (most blocks touch none, or only walls).
+    // Strong coupling reads the step's mask (k_body_touch) and leaves untouched blocks
+    // at once, writing nothing: the apply kernel skips their partials.  The weak path
+    // finds the mask here and writes zero partials for untouched bodies.
+    unsigned long long touched;
+    if (INC) {
+        touched = P.blk_touch[blockIdx.x];
+        if (touched == 0ull) return;  // uniform per block
+    } else {
+        __shared__ unsigned long long s_mask;
+        if (threadIdx.x == 0) s_mask = 0ull;
+        __syncthreads();
+        unsigned long long mine = 0ull;
+        for (int t = c.s; t < nb; t += T) {
+            const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * NF + i]];
+            if (k >= 0) mine |= 1ull << k;
+        }
+        if (mine) atomicOr(&s_mask, mine);
+        __syncthreads();
+        touched = s_mask;
     }
-    if (mine) atomicOr(&s_mask, mine);
-    __syncthreads();
-    const unsigned long long touched = s_mask;
     // the particle's own state is needed only in blocks that touch a body, and there only
     // by particles with boundary neighbours
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -145,11 +153,38 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
                 f[5] += rx * Fy - ry * Fx;
             }
         }
+        if (INC && !any) continue;   // the apply kernel skips this block for body k
         for (int a = 0; a < 6; ++a) {
             double t = any ? block_sum_d(f[a], sh) : 0.0;
             if (threadIdx.x == 0) P.body_partial[((int64_t)(sc.body_off + k) * 6 + a) * P.ntblk + blockIdx.x] = t;
         }
     }
+}
+
+// Strong coupling: the bodies each sweep block's particles touch, once per step (positions
+// and neighbour lists are fixed from the density sweep to the advection), as a bit mask of
+// the scene's bodies; blocks of other scenes get 0.
+template <int T>
+__global__ void __launch_bounds__(kBlock) k_body_touch(Ptrs P)
+{
+    __shared__ unsigned long long s_mask;
+    kernel_enter(P.ctl, KID_BTOUCH);
+    const Lane<T> c = lane_ctx<T>(P);
+    const SceneDev &sc = *c.sc;
+    if (threadIdx.x == 0) s_mask = 0ull;
+    __syncthreads();
+    if (sc.strong && sc.nbody > 0) {   // uniform per block
+        const int64_t NF = P.NF;
+        const int nb = c.valid ? P.nnb[c.i] : 0;
+        unsigned long long mine = 0ull;
+        for (int t = c.s; t < nb; t += T) {
+            const int32_t k = P.bbody_s[P.bnbr[(int64_t)t * NF + c.i]];
+            if (k >= 0) mine |= 1ull << k;
+        }
+        if (mine) atomicOr(&s_mask, mine);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) P.blk_touch[blockIdx.x] = s_mask;
 }
 
 // Sum of one body's force or torque component over its scene's sweep blocks, in block
@@ -190,10 +225,16 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P)
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];
     if (!sc.strong) return;
+    // the partials of the blocks that touch this body, in block order (thread t takes
+    // blocks t, t + 256, ...; the other blocks contribute nothing)
+    const int k = body - sc.body_off;
+    double f[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < sc.tblk_count; q += 256) {
+        if (!((P.blk_touch[sc.tblk_first + q] >> k) & 1ull)) continue;
+        for (int a = 0; a < 6; ++a) f[a] += P.body_partial[((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first + q];
+    }
     for (int a = 0; a < 6; ++a) {
-        const double *part = P.body_partial + ((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first;
-        double t = 0.0;
-        for (int q = threadIdx.x; q < sc.tblk_count; q += 256) t += part[q];
+        double t = f[a];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         __syncthreads();
@@ -249,6 +290,14 @@ __global__ void __launch_bounds__(kBlock) k_boundary_vel(Ptrs P)
 }
 
 }  // namespace
+
+void launch_body_touch(const Ptrs &P, cudaStream_t s)
+{
+    if (!P.ntblk || !P.nbodies_total) return;
+#define SPH_L(T) k_body_touch<T><<<P.ntblk, kBlock, 0, s>>>(P)
+    SPH_BY_LANES(P, SPH_L);
+#undef SPH_L
+}
 
 void launch_strong_update(const Ptrs &P, cudaStream_t s)
 {
