@@ -329,6 +329,45 @@ sph_status sph_mlp_train(const float *features, const float *labels, int64_t n, 
                          float *adam_state, int32_t epochs, int32_t batch, float lr, uint64_t seed,
                          float *loss_history, int32_t *error, void *stream);
 
+/* Kernel ids of the device trace (sph_set_trace / sph_read_trace). */
+#define SPH_KID_STEP_BEGIN 1      /* step begin */
+#define SPH_KID_KEY_HIST_F 2      /* fluid cell-key histogram */
+#define SPH_KID_KEY_HIST_B 3      /* boundary cell-key histogram */
+#define SPH_KID_SCAN 4            /* look-back scan */
+#define SPH_KID_SCATTER_F 5       /* fluid scatter */
+#define SPH_KID_SCATTER_B 6       /* boundary scatter */
+#define SPH_KID_RANK_F 7          /* fluid rank and gather */
+#define SPH_KID_RANK_B 8          /* boundary rank and gather */
+#define SPH_KID_DENSITY 9         /* density, alpha, lists */
+#define SPH_KID_PASS_A0 10        /* divergence pass A */
+#define SPH_KID_PASS_A1 11        /* density pass A */
+#define SPH_KID_PASS_B0 12        /* divergence pass B */
+#define SPH_KID_PASS_B1 13        /* density pass B */
+#define SPH_KID_PASS_B0W 14       /* divergence warm start */
+#define SPH_KID_PASS_B1W 15       /* density warm start / EOS */
+#define SPH_KID_NONP 16           /* non-pressure forces */
+#define SPH_KID_WARM 17           /* warm-start gate and features */
+#define SPH_KID_ADVECT 18         /* advection */
+#define SPH_KID_STEP_END 19       /* step end, rigid integration */
+#define SPH_KID_SET_DT 20         /* fixed step */
+#define SPH_KID_BUPDATE 21        /* boundary pose update */
+#define SPH_KID_PSI 22            /* boundary Psi */
+#define SPH_KID_BFORCE 23         /* body force (weak) */
+#define SPH_KID_BREDUCE 24        /* body force reduction */
+#define SPH_KID_CG_INIT 25        /* CG initial residual */
+#define SPH_KID_CG_AP 26          /* CG matrix sweep */
+#define SPH_KID_CG_XR 27          /* CG update */
+#define SPH_KID_CG_P 28           /* CG direction */
+#define SPH_KID_MLP_WARM 29       /* warm-start network */
+#define SPH_KID_BFORCE_INC 30     /* body force (strong) */
+#define SPH_KID_BAPPLY 31         /* body impulse (strong) */
+#define SPH_KID_BVEL 32           /* boundary velocities (strong) */
+#define SPH_KID_CHECK0 33         /* divergence convergence test */
+#define SPH_KID_CHECK1 34         /* density convergence test */
+#define SPH_KID_CG_ALPHA 35       /* CG alpha */
+#define SPH_KID_CG_BETA 36        /* CG beta and stopping test */
+#define SPH_KID_BTOUCH 37         /* bodies touched per block (strong) */
+
 /* Device trace for profiling graph replays: with capacity > 0 every kernel's first thread
  * records (globaltimer_ns << 8 | kernel id) in a device ring of that many entries (the
  * library allocates it; 0 turns tracing off and frees it).  sph_read_trace copies up to

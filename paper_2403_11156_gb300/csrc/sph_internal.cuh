@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "sph.h"
 
 namespace sph {
 
@@ -155,6 +156,44 @@ enum KernelId : uint32_t {
     KID_CG_BETA = 36,
     KID_BTOUCH = 37
 };
+
+static_assert(KID_STEP_BEGIN == SPH_KID_STEP_BEGIN, "trace id");
+static_assert(KID_KEY_HIST_F == SPH_KID_KEY_HIST_F, "trace id");
+static_assert(KID_KEY_HIST_B == SPH_KID_KEY_HIST_B, "trace id");
+static_assert(KID_SCAN == SPH_KID_SCAN, "trace id");
+static_assert(KID_SCATTER_F == SPH_KID_SCATTER_F, "trace id");
+static_assert(KID_SCATTER_B == SPH_KID_SCATTER_B, "trace id");
+static_assert(KID_RANK_F == SPH_KID_RANK_F, "trace id");
+static_assert(KID_RANK_B == SPH_KID_RANK_B, "trace id");
+static_assert(KID_DENSITY == SPH_KID_DENSITY, "trace id");
+static_assert(KID_PASS_A0 == SPH_KID_PASS_A0, "trace id");
+static_assert(KID_PASS_A1 == SPH_KID_PASS_A1, "trace id");
+static_assert(KID_PASS_B0 == SPH_KID_PASS_B0, "trace id");
+static_assert(KID_PASS_B1 == SPH_KID_PASS_B1, "trace id");
+static_assert(KID_PASS_B0W == SPH_KID_PASS_B0W, "trace id");
+static_assert(KID_PASS_B1W == SPH_KID_PASS_B1W, "trace id");
+static_assert(KID_NONP == SPH_KID_NONP, "trace id");
+static_assert(KID_WARM == SPH_KID_WARM, "trace id");
+static_assert(KID_ADVECT == SPH_KID_ADVECT, "trace id");
+static_assert(KID_STEP_END == SPH_KID_STEP_END, "trace id");
+static_assert(KID_SET_DT == SPH_KID_SET_DT, "trace id");
+static_assert(KID_BUPDATE == SPH_KID_BUPDATE, "trace id");
+static_assert(KID_PSI == SPH_KID_PSI, "trace id");
+static_assert(KID_BFORCE == SPH_KID_BFORCE, "trace id");
+static_assert(KID_BREDUCE == SPH_KID_BREDUCE, "trace id");
+static_assert(KID_CG_INIT == SPH_KID_CG_INIT, "trace id");
+static_assert(KID_CG_AP == SPH_KID_CG_AP, "trace id");
+static_assert(KID_CG_XR == SPH_KID_CG_XR, "trace id");
+static_assert(KID_CG_P == SPH_KID_CG_P, "trace id");
+static_assert(KID_MLP_WARM == SPH_KID_MLP_WARM, "trace id");
+static_assert(KID_BFORCE_INC == SPH_KID_BFORCE_INC, "trace id");
+static_assert(KID_BAPPLY == SPH_KID_BAPPLY, "trace id");
+static_assert(KID_BVEL == SPH_KID_BVEL, "trace id");
+static_assert(KID_CHECK0 == SPH_KID_CHECK0, "trace id");
+static_assert(KID_CHECK1 == SPH_KID_CHECK1, "trace id");
+static_assert(KID_CG_ALPHA == SPH_KID_CG_ALPHA, "trace id");
+static_assert(KID_CG_BETA == SPH_KID_CG_BETA, "trace id");
+static_assert(KID_BTOUCH == SPH_KID_BTOUCH, "trace id");
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
 __device__ __forceinline__ void kernel_enter(Control *ctl, uint32_t id)

@@ -87,3 +87,11 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(sph, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         sph.load()
+
+
+def test_trace_kernel_ids_match_header():
+    # the binding names trace entries by the header's SPH_KID_* values
+    text = open(os.path.join(ROOT, "include", "sph.h")).read()
+    ids = {int(v): k for k, v in re.findall(r"#define SPH_(KID_\w+) (\d+)", text)}
+    assert sorted(ids) == list(range(1, len(ids) + 1))
+    assert sorted(sph.KERNEL_IDS) == sorted(ids)
