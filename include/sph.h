@@ -376,6 +376,13 @@ sph_status sph_mlp_train(const float *features, const float *labels, int64_t n, 
 sph_status sph_set_trace(sph_ctx *ctx, int32_t capacity);
 sph_status sph_read_trace(sph_ctx *ctx, uint64_t *out, int32_t cap, int32_t *n, int32_t reset);
 
+/* Failure-path probe: enqueues one thread that waits, spin_limit times about 1 us each, on a
+ * device flag that nothing sets.  The wait runs out and records a device error, so the next
+ * sph_synchronize returns SPH_ETIMEOUT and the context is poisoned (only sph_destroy stays
+ * valid), as after any bounded device wait of the library that gave up.  For tests of the
+ * error path; it neither faults nor hangs the GPU.  spin_limit: 1..10^6, else SPH_EINVAL. */
+sph_status sph_probe_wait_timeout(sph_ctx *ctx, int32_t spin_limit);
+
 /* Kernel launches enqueued since creation (counted on the device for graph replays). */
 sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
 

@@ -232,6 +232,18 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
 }
 
 // ------------------------------------------------------------------ read / write kernels
+// One thread waits on a flag that nothing sets, a bounded number of times; when the wait
+// runs out it records the same error as the library's other bounded waits.
+__global__ void k_probe_wait(Control *ctl, uint32_t limit)
+{
+    const volatile uint32_t *flag = &ctl->probe_flag;
+    for (uint32_t k = 0; k < limit; ++k) {
+        if (*flag != 0u) return;
+        __nanosleep(1000);
+    }
+    atomicExch(&ctl->error, 6);
+}
+
 __global__ void k_read_fluid(Ptrs P, int scene, int field, void *out)
 {
     const SceneDev &sc = P.scenes[scene];
@@ -1183,6 +1195,15 @@ sph_status sph_steps(sph_ctx *c, int32_t n, float dt)
         if (st != SPH_OK) return st;
     }
     return SPH_OK;
+}
+
+sph_status sph_probe_wait_timeout(sph_ctx *c, int32_t spin_limit)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (spin_limit < 1 || spin_limit > 1000000) return fail(c, SPH_EINVAL, "spin_limit (1..10^6)");
+    k_probe_wait<<<1, 1, 0, c->stream>>>(c->P.ctl, (uint32_t)spin_limit);
+    return check_async(c);
 }
 
 sph_status sph_synchronize(sph_ctx *c)

@@ -100,7 +100,7 @@ struct ScanCtl {
 
 // Context-wide control words (device).
 struct Control {
-    uint32_t pad_c;
+    uint32_t probe_flag;              // never set: the wait of sph_probe_wait_timeout
     uint32_t loop_flag;               // host-readable copy of the loop condition
     uint32_t loop_guard;              // iterations of the current loop
     uint32_t pad0;

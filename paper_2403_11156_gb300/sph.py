@@ -145,6 +145,7 @@ def load():
     L.sph_synchronize.argtypes = [vp]
     L.sph_read_state.argtypes = [vp, ip, vp, vp, vp, vp, ip]
     L.sph_write_state.argtypes = [vp, ip, vp, vp, vp, vp, ip]
+    L.sph_probe_wait_timeout.argtypes = [vp, ip]
     L.sph_read_field.argtypes = [vp, ip, ip, vp, ip]
     L.sph_get_stats.argtypes = [vp, ip, C.POINTER(Stats)]
     L.sph_read_bodies.argtypes = [vp, ip, dp]
@@ -169,7 +170,7 @@ def load():
                                    C.POINTER(C.c_int64), vp]
     L.sph_render_heightmap.argtypes = [vp, ip, fp, fp, ip, ip, C.c_float, vp]
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
-                 "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats",
+                 "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats", "sph_probe_wait_timeout",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
                  "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
                  "sph_read_trace", "sph_surface_field", "sph_surface_mesh", "sph_render_heightmap"):
@@ -382,6 +383,11 @@ class Context:
         _check(self.ctx, load().sph_read_bodies(self.ctx, scene,
                                                 out.ctypes.data_as(C.POINTER(C.c_double))))
         return out[:nb]
+
+    def sph_probe_wait_timeout(self, spin_limit=1000):
+        """Enqueue a bounded wait that runs out (the device error path); returns the status
+        of the enqueue, the next synchronize reports SPH_ETIMEOUT."""
+        return load().sph_probe_wait_timeout(self.ctx, int(spin_limit))
 
     def sph_set_mode(self, graph=True, timing=False):
         _check(self.ctx, load().sph_set_mode(self.ctx, int(graph), int(timing)))

@@ -128,3 +128,34 @@ def test_enqueue_only_read_matches_synchronous_read():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(x.cpu().numpy(), g.sph_read_state()[0])
 
+
+
+def test_bounded_wait_that_runs_out_reports_timeout():
+    """A device wait that runs out (the probe waits on a flag that nothing sets, about 200 us)
+    is reported as SPH_ETIMEOUT and poisons the context; the GPU stays usable for a new one.
+    No kernel faults, traps or hangs."""
+    d = _small()
+    g = gpu_ctx(d)
+    g.sph_step(DT)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    assert g.sph_probe_wait_timeout(200) == sph.SPH_OK
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_ETIMEOUT
+    with pytest.raises(sph.SphError):
+        g.sph_step(DT)
+    g.close()
+    h = gpu_ctx(d)
+    h.sph_step(DT)
+    assert h.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+
+
+def test_nonfinite_state_reported():
+    # a NaN velocity written into the state (host-side injection) is caught after the step
+    d = _small()
+    g = gpu_ctx(d)
+    g.sph_step(DT)
+    _, v, _, _ = g.sph_read_state()
+    v = v.copy()
+    v[5] = np.nan
+    g.sph_write_state(v=v)
+    g.sph_step(DT)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_ENUMERIC
