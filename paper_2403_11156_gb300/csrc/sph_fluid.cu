@@ -8,9 +8,8 @@
 // step (divergence and density Jacobi passes, non-pressure forces, warm starts) gathers
 // through that list, lane s taking entries s, s + T, ..., and combines the T partial sums
 // with warp shuffles.  The solvers' error sums are accumulated per block in FP64 by pass A,
-// folded eight at a time by pass B and summed in a fixed order by a one-block check
-// kernel, which also decides the loop condition on the device (CUDA graph conditional
-// node).
+// folded by pass B and summed in a fixed order by a one-block check kernel, which also
+// decides the loop condition on the device (CUDA graph conditional node).
 #include <math_constants.h>
 
 #include <type_traits>
@@ -68,9 +67,11 @@ __device__ __forceinline__ int warp_max(int v)
 }
 
 // Fixed-order block sum of one double per thread (deterministic).
-// Pass A's error partials are folded kFold at a time by pass B's blocks before its last
-// block sums the folds.
-constexpr int kFold = 8;
+// Pass A's error partials are folded by pass B's blocks, fold_size(count) consecutive ones
+// per fold (at least 8, and at most 256 folds per scene), and the check kernel sums a
+// scene's folds with one warp.  The order depends only on the scene's own block count, so
+// a scene reduces the same way alone and in any batch.
+__device__ __forceinline__ int32_t fold_size(int32_t count) { return max(8, (count + 255) / 256); }
 
 __device__ double block_sum(double v, double *sh)
 {
@@ -453,12 +454,13 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P)
         }
     }
     if (WARM) return;
-    // fold pass A's error partials: the scene's first ceil(count / kFold) blocks each sum
-    // kFold consecutive ones in block order (the check kernel, a later launch, sums the folds)
+    // fold pass A's error partials: the scene's first ceil(count / F) blocks each sum F
+    // consecutive ones in block order (the check kernel, a later launch, sums the folds)
     if (run && threadIdx.x == 0) {
         const int32_t lb = (int32_t)blockIdx.x - sc.tblk_first;
-        if (lb < (sc.tblk_count + kFold - 1) / kFold) {
-            const int32_t k0 = lb * kFold, k1 = min(k0 + kFold, sc.tblk_count);
+        const int32_t F = fold_size(sc.tblk_count);
+        if (lb < (sc.tblk_count + F - 1) / F) {
+            const int32_t k0 = lb * F, k1 = min(k0 + F, sc.tblk_count);
             double t = 0.0;
             for (int32_t k = k0; k < k1; ++k) t += __ldcg(P.partial + sc.tblk_first + k);
             P.partial2[blockIdx.x] = t;
@@ -467,65 +469,40 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P)
 }
 
 // Convergence test of one Jacobi iteration (Alg. ppe_solver's loop condition), one block
-// of 1024 threads after pass B.  A scene's folds are summed in a fixed order: with a few
-// scenes the whole block takes each in turn (thread t sums folds t, t + 1024, ..., then a
-// fixed tree), with many one warp per scene (lane l sums folds l, l + 32, ..., then a
-// butterfly).  The sum gives the mean error; the iteration counters advance and the loop
-// condition is set for the host and for the CUDA graph's while node.
-__device__ __forceinline__ void finish_iteration(const SceneDev &qd, SceneState &qs, int S, double total, int *s_any)
-{
-    double err = qd.nf > 0 ? total / (double)qd.nf / (double)qd.rho0 : 0.0;
-    if (S == 0) err *= (double)qs.dt;
-    if (qs.it[S] == 0) qs.err0[S] = err;
-    qs.err[S] = err;
-    qs.it[S] += 1;
-    qs.total_it[S] += 1;
-    if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
-    if (solver_active(qd, qs, S)) atomicOr(s_any, 1);
-}
-
+// after pass B: one warp per scene (32 scenes at a time) sums the scene's folds in a fixed
+// order (lane l takes folds l, l + 32, ..., then a butterfly), which gives the mean error;
+// the iteration counters advance and the loop condition is set for the host and for the
+// CUDA graph's while node.
 constexpr int kCheckThreads = 1024;
-constexpr int kCheckBlockWideScenes = 4;   // up to this many scenes: block-wide sums
 
 template <int S>
 __global__ void __launch_bounds__(kCheckThreads) k_solver_check(Ptrs P, cudaGraphConditionalHandle handle,
                                                                int use_handle)
 {
     __shared__ int s_any;
-    __shared__ double sh[kCheckThreads / 32];
     kernel_enter(P.ctl, KID_CHECK0 + S);
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (P.nscenes <= kCheckBlockWideScenes) {
-        for (int q = 0; q < P.nscenes; ++q) {
-            const SceneDev &qd = P.scenes[q];
-            SceneState &qs = P.st[q];
-            if (!solver_active(qd, qs, S)) continue;   // uniform: nothing wrote qs yet
-            const int32_t nfold = (qd.tblk_count + kFold - 1) / kFold;
-            double t = 0.0;
-            for (int k = threadIdx.x; k < nfold; k += kCheckThreads) t += __ldcg(P.partial2 + qd.tblk_first + k);
-            t = warp_sum(t);
-            if (lane == 0) sh[warp] = t;
-            __syncthreads();
-            if (warp == 0) {
-                double u = sh[lane];
-                u = warp_sum(u);
-                if (lane == 0) finish_iteration(qd, qs, S, u, &s_any);
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int q = warp; q < P.nscenes; q += kCheckThreads / 32) {
-            const SceneDev &qd = P.scenes[q];
-            SceneState &qs = P.st[q];
-            if (!solver_active(qd, qs, S)) continue;   // its pass A and B did not run
-            const int32_t nfold = (qd.tblk_count + kFold - 1) / kFold;
-            double t = 0.0;
-#pragma unroll 4
-            for (int k = lane; k < nfold; k += 32) t += __ldcg(P.partial2 + qd.tblk_first + k);
-            t = warp_sum(t);
-            if (lane == 0) finish_iteration(qd, qs, S, t, &s_any);
+    for (int q = warp; q < P.nscenes; q += kCheckThreads / 32) {
+        const SceneDev &qd = P.scenes[q];
+        SceneState &qs = P.st[q];
+        if (!solver_active(qd, qs, S)) continue;   // its pass A and B did not run
+        const int32_t F = fold_size(qd.tblk_count);
+        const int32_t nfold = (qd.tblk_count + F - 1) / F;
+        double t = 0.0;
+#pragma unroll 8
+        for (int k = lane; k < nfold; k += 32) t += __ldcg(P.partial2 + qd.tblk_first + k);
+        t = warp_sum(t);
+        if (lane == 0) {
+            double err = qd.nf > 0 ? t / (double)qd.nf / (double)qd.rho0 : 0.0;
+            if (S == 0) err *= (double)qs.dt;
+            if (qs.it[S] == 0) qs.err0[S] = err;
+            qs.err[S] = err;
+            qs.it[S] += 1;
+            qs.total_it[S] += 1;
+            if (!solver_active(qd, qs, S) && qs.err[S] > (double)qd.eta[S]) qs.flags |= 2;
+            if (solver_active(qd, qs, S)) atomicOr(&s_any, 1);
         }
     }
     __syncthreads();

@@ -145,56 +145,39 @@ constexpr int kReduceThreads = 1024;
 
 // One block (kReduceThreads threads) sums, per scene with an active CG, the block partials
 // of the preceding launch over the scene's sweep blocks (SWEEP) or fluid blocks, in a fixed
-// order: with a few scenes the whole block takes each in turn, with many one warp per
-// scene.  done(scene, a, b) runs in one thread per scene.
+// order that depends only on the scene (thread t takes partials t, t + 1024, ..., then a
+// fixed tree), so a scene reduces the same way alone and in any batch; the scenes go in
+// turn.  done(scene, a, b) runs in one thread per scene.
 template <bool SWEEP, typename F>
 __device__ void reduce_scenes(const Ptrs &P, double *sh, F &&done)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double2 *d = reinterpret_cast<const double2 *>(P.cg_dots);
-    if (P.nscenes <= 4) {
-        for (int q = 0; q < P.nscenes; ++q) {
-            const SceneDev &qd = P.scenes[q];
-            if (!cg_active(qd, P.st[q])) continue;   // uniform: nothing wrote the state yet
-            const int32_t first = SWEEP ? qd.tblk_first : qd.fblk_first;
-            const int32_t count = SWEEP ? qd.tblk_count : qd.fblk_count;
-            double a = 0.0, b = 0.0;
-            for (int k = threadIdx.x; k < count; k += kReduceThreads) {
-                const double2 v = __ldcg(d + first + k);
-                a += v.x;
-                b += v.y;
-            }
-            a = warp_sum(a);
-            b = warp_sum(b);
-            if (lane == 0) {
-                sh[2 * warp] = a;
-                sh[2 * warp + 1] = b;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                double u = sh[2 * lane], w = sh[2 * lane + 1];
-                u = warp_sum(u);
-                w = warp_sum(w);
-                if (lane == 0) done(q, u, w);
-            }
-            __syncthreads();
+    for (int q = 0; q < P.nscenes; ++q) {
+        const SceneDev &qd = P.scenes[q];
+        if (!cg_active(qd, P.st[q])) continue;   // uniform: nothing wrote the state yet
+        const int32_t first = SWEEP ? qd.tblk_first : qd.fblk_first;
+        const int32_t count = SWEEP ? qd.tblk_count : qd.fblk_count;
+        double a = 0.0, b = 0.0;
+        for (int k = threadIdx.x; k < count; k += kReduceThreads) {
+            const double2 v = __ldcg(d + first + k);
+            a += v.x;
+            b += v.y;
         }
-    } else {
-        for (int q = warp; q < P.nscenes; q += kReduceThreads / 32) {
-            const SceneDev &qd = P.scenes[q];
-            if (!cg_active(qd, P.st[q])) continue;
-            const int32_t first = SWEEP ? qd.tblk_first : qd.fblk_first;
-            const int32_t count = SWEEP ? qd.tblk_count : qd.fblk_count;
-            double a = 0.0, b = 0.0;
-            for (int k = lane; k < count; k += 32) {
-                const double2 v = __ldcg(d + first + k);
-                a += v.x;
-                b += v.y;
-            }
-            a = warp_sum(a);
-            b = warp_sum(b);
-            if (lane == 0) done(q, a, b);
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (lane == 0) {
+            sh[2 * warp] = a;
+            sh[2 * warp + 1] = b;
         }
+        __syncthreads();
+        if (warp == 0) {
+            double u = sh[2 * lane], w = sh[2 * lane + 1];
+            u = warp_sum(u);
+            w = warp_sum(w);
+            if (lane == 0) done(q, u, w);
+        }
+        __syncthreads();
     }
 }
 

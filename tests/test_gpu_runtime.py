@@ -159,3 +159,22 @@ def test_nonfinite_state_reported():
     g.sph_write_state(v=v)
     g.sph_step(DT)
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_ENUMERIC
+
+
+def test_large_batch_equals_single():
+    """More scenes than one warp of the convergence check's block handles at once and an
+    implicit-viscosity scene: every reduction order depends on the scene alone, so each scene
+    of the batch steps bit-identically to the scene alone."""
+    ds = [scenes.dam_break_small(seed=11 + k, n=(6 + k, 7, 5 + 2 * k), box=0.4) for k in range(5)]
+    ds.append(_small(seed=17, viscosity=0.05, viscosity_mode=scenes.VISC_IMPLICIT))
+    batch = gpu_ctx(ds)
+    batch.sph_steps(5, DT)
+    for k, d in enumerate(ds):
+        single = gpu_ctx(d)
+        single.sph_steps(5, DT)
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w)
+        sb, ss = batch.sph_get_stats(k), single.sph_get_stats()
+        assert sb["total_dens_iters"] == ss["total_dens_iters"]
+        assert sb["total_div_iters"] == ss["total_div_iters"]
+        assert sb["cg_iters"] == ss["cg_iters"]
