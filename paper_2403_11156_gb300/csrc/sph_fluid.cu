@@ -123,10 +123,11 @@ __global__ void k_step_begin(Ptrs P)
 // ------------------------------------------------------------------------------------
 // Density (Eq. density + Sec. 3.5 boundary term), DFSPH alpha, neighbour lists, and the
 // gate of the divergence warm start (D rho/Dt with the velocities at step start).
-// Nine resident blocks per SM: 56 registers without spills (left to itself the compiler
-// picks 48 and spills; measured 4 % slower on the 1.2M scene).
+// Nine resident blocks per SM with one lane (56 registers; left to itself the compiler picks
+// 48 and spills, measured 4 % slower on the 1.2M scene), eight with several (64 registers
+// for the batched cooperative append).
 template <int T>
-__global__ void __launch_bounds__(kBlock, 9) k_density_alpha(Ptrs P)
+__global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P)
 {
     kernel_enter(P.ctl, KID_DENSITY);
     const Lane<T> c = lane_ctx<T>(P);
@@ -206,17 +207,36 @@ __global__ void __launch_bounds__(kBlock, 9) k_density_alpha(Ptrs P)
                     if (dz == 0 && dy == 0) scan(std::true_type{});
                     else scan(std::false_type{});
                 } else {
-                    for (uint32_t j0 = jb; j0 < je; j0 += (uint32_t)T) {   // uniform in the group
+                    // the group's lanes test T consecutive candidates at a time and append the
+                    // hits in candidate order; full batches of kCand groups load all their
+                    // candidates before the first test (one memory latency per batch)
+                    auto append = [&](uint32_t j, bool hit) {
+                        const unsigned bits = __ballot_sync(gmask, hit) >> gshift;
+                        const int slot = nn_f + __popc(bits & below);
+                        if (hit && slot < cap_f) P.nbr[(int64_t)slot * NF + i] = (int32_t)j;
+                        nn_f += __popc(bits);
+                    };
+                    constexpr int kCand = 4;
+                    uint32_t j0 = jb;
+                    for (; j0 + (uint32_t)(kCand * T) <= je; j0 += (uint32_t)(kCand * T)) {   // uniform in the group
+                        float4 pc[kCand];
+#pragma unroll
+                        for (int u = 0; u < kCand; ++u) pc[u] = __ldg(P.pos_s + j0 + (uint32_t)(u * T + s));
+#pragma unroll
+                        for (int u = 0; u < kCand; ++u) {
+                            const uint32_t j = j0 + (uint32_t)(u * T + s);
+                            float dx, dy2, dz2;
+                            append(j, pred_d2(pi, pc[u], dx, dy2, dz2) < h2 && j != self);
+                        }
+                    }
+                    for (; j0 < je; j0 += (uint32_t)T) {   // uniform in the group
                         const uint32_t j = j0 + (uint32_t)s;
                         bool hit = false;
                         if (j < je) {
                             float dx, dy2, dz2;
                             hit = pred_d2(pi, __ldg(P.pos_s + j), dx, dy2, dz2) < h2 && j != self;
                         }
-                        const unsigned bits = __ballot_sync(gmask, hit) >> gshift;
-                        const int slot = nn_f + __popc(bits & below);
-                        if (hit && slot < cap_f) P.nbr[(int64_t)slot * NF + i] = (int32_t)j;
-                        nn_f += __popc(bits);
+                        append(j, hit);
                     }
                 }
                 if (sc.nb > 0) {
