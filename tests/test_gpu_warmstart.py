@@ -130,3 +130,19 @@ def test_learned_batch_equals_single(trained):
             np.testing.assert_array_equal(u, w)
         np.testing.assert_array_equal(batch.sph_read_field(sph.FIELD_KAPPA0, k), single.sph_read_field(sph.FIELD_KAPPA0))
         assert batch.sph_get_stats(k)["total_dens_iters"] == single.sph_get_stats()["total_dens_iters"]
+
+
+def test_trained_network_needs_fewer_iterations():
+    """What the trained network gains: trained on the GPU on 40k solver states of two
+    seeded 200k-300k dam breaks, it warm-starts an unseen 200k dam break (CFL steps, 0.1 %
+    tolerance, 150 steps from rest) with fewer density iterations than the previous-step and
+    the zero warm starts (measured 2.73 against 3.65 and 6.11), at the same tolerance."""
+    f, y = warmstart.generate_dataset(40_000, 80, n_scenes=2, size_range=(2e5, 3e5))
+    params, hist = warmstart.train(f, y, epochs=30)
+    assert hist[-1] < 0.5 * hist[0]
+    res = warmstart.compare_warm_starts(scenes.dam_break_random(99, 200_000), params, steps=150)
+    for mode in ("zero", "previous", "learned"):
+        assert res[mode]["final_error"] <= 1e-3
+    learned, previous, zero = (res[m]["density_iters_per_step"] for m in ("learned", "previous", "zero"))
+    assert learned <= 0.85 * previous and learned <= 0.6 * zero
+    assert res["learned"]["divergence_iters_per_step"] <= 1.1 * res["previous"]["divergence_iters_per_step"]
