@@ -66,13 +66,13 @@ __device__ __forceinline__ int warp_max(int v)
     return v;
 }
 
-// Fixed-order block sum of one double per thread (deterministic).
 // Pass A's error partials are folded by pass B's blocks, fold_size(count) consecutive ones
 // per fold (at least 8, and at most 256 folds per scene), and the check kernel sums a
 // scene's folds with one warp.  The order depends only on the scene's own block count, so
 // a scene reduces the same way alone and in any batch.
 __device__ __forceinline__ int32_t fold_size(int32_t count) { return max(8, (count + 255) / 256); }
 
+// Fixed-order block sum of one double per thread (deterministic).
 __device__ double block_sum(double v, double *sh)
 {
     v = warp_sum(v);
@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
         set_w(P.pos_s, i, kappa / rho);
         e = (double)ei;
     }
-    // the block's FP64 error partial; the pass B that follows reduces the partials in a
-    // fixed order (no last-block step here: pass A only has to finish)
+    // the block's FP64 error partial; pass B folds the partials and the check kernel sums
+    // the folds in a fixed order (no last-block step here: pass A only has to finish)
     const double bsum = block_sum(e, sh);
     if (threadIdx.x == 0) P.partial[blockIdx.x] = bsum;
 }
