@@ -9,6 +9,13 @@ each step's result (positions) copied to pinned host memory; `roofline` reports 
 dominant kernel from a second pass of eager, CUDA-event-timed steps; `cpu_baseline` times
 the CPU oracle on a bounded sample.  With N > 1 (torchrun) every rank runs an
 independent replica of the scene (the scene does not shard; scaling is weak).
+
+Secondary sections of the same line (rank 0; `--no-learned`, `--no-batched` skip them):
+`learned_vs_plain` (the warm-start network trained in the run, then zero / previous-step /
+learned warm starts on the 8k and the 1.2M dam breaks and the 64-scene batch),
+`batched_64_scenes` (sharded over the ranks), `wcsph_1.2M`, `solvers_8k` (DFSPH, PCISPH,
+WCSPH), `viscous_column_250k` (implicit viscosity), `coupling_1.2M` (weak vs strong) and
+`post_processing_1.2M`.
 """
 from __future__ import annotations
 
