@@ -416,9 +416,11 @@ sph_status sph_grid_order_noalloc(const float *x, int64_t n, const float *domain
  * (the SPH interpolant of Sec. 3.2 applied to 1: about 1 inside, 0 outside) at the grid
  * nodes origin + spacing (i, j, k), 0 <= i < dims[0] ..., for scene `scene` at its
  * current positions, rho_j the density of the last step (rho0 before the first step).
- * field: device float [dims[2]][dims[1]][dims[0]].  Enqueued on the context's stream;
- * returns after enqueueing.  The reconstruction of a surface is the iso-level 0.5 of
- * this field (sph_surface_mesh). */
+ * field: device float [dims[2]][dims[1]][dims[0]], caller-owned.  Enqueued on the
+ * context's stream; returns after enqueueing.  The reconstruction of a surface is the
+ * iso-level 0.5 of this field (sph_surface_mesh).  SPH_EINVAL for a scene out of range,
+ * NULL pointers, a spacing that is not positive and finite, dims < 1, a non-finite origin
+ * or more than 2^31 nodes; SPH_ECUDA if scratch cannot be allocated. */
 sph_status sph_surface_field(sph_ctx *ctx, int32_t scene, const float origin[3], float spacing,
                              const int32_t dims[3], float *field);
 
@@ -429,7 +431,9 @@ sph_status sph_surface_field(sph_ctx *ctx, int32_t scene, const float origin[3],
  * the normal pointing from phi > iso towards phi <= iso (outward for a fluid).  tris:
  * device float [cap][3][3], triangles in cube order (x fastest); *n_tris (host) receives
  * the total, which may exceed cap (then only cap triangles are written and SPH_EOVERFLOW
- * is returned).  Enqueued on stream, which the call synchronises. */
+ * is returned).  Enqueued on stream, which the call synchronises.  SPH_EINVAL for NULL
+ * pointers (tris may be NULL with cap = 0, to count), cap < 0, dims < 2, a spacing that is
+ * not positive and finite, or a non-finite iso or origin. */
 sph_status sph_surface_mesh(const float *field, const int32_t dims[3], const float origin[3],
                             float spacing, float iso, float *tris, int64_t cap, int64_t *n_tris,
                             void *stream);
@@ -437,8 +441,10 @@ sph_status sph_surface_mesh(const float *field, const int32_t dims[3], const flo
 /* Headless orthographic height map of scene `scene` viewed down the -z axis: pixel (i, j)
  * (centre lo + ((i + 0.5)(hi - lo)_x / width, (j + 0.5)(hi - lo)_y / height)) receives the
  * largest z + sqrt(radius^2 - d^2) over particles whose disk of the given radius covers
- * it (d < radius), NaN where none does.  out: device float [height][width].  Enqueued on
- * the context's stream; returns after enqueueing. */
+ * it (d < radius), NaN where none does.  out: device float [height][width], caller-owned.
+ * Enqueued on the context's stream; returns after enqueueing.  SPH_EINVAL for a scene out
+ * of range, NULL pointers, width or height < 1 or more than 2^31 pixels, or a bad view
+ * rectangle or radius. */
 sph_status sph_render_heightmap(sph_ctx *ctx, int32_t scene, const float lo[2], const float hi[2],
                                 int32_t width, int32_t height, float radius, float *out);
 
