@@ -263,8 +263,8 @@ sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
  * candidate on temporary contexts, twice, keeping each candidate's faster time (the
  * default configuration is kept unless a candidate is more than 3 % faster); the choice
  * is cached per process for the same device and workload size (log2 of the fluid count,
- * scene count, bodies, viscosity mode, lanes_per_particle).  Neighbour sets do not depend on the choice; the summation order,
- * and so the last bits of FP32 results, may. */
+ * scene count, bodies, viscosity mode, lanes_per_particle).  Neighbour sets do not
+ * depend on the choice; the summation order, and so the last bits of FP32 results, may. */
 typedef struct sph_tuning {
     int32_t tuned;            /* 1 if this context was autotuned                     */
     int32_t from_cache;       /* the choice came from the per-process cache          */
