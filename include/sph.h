@@ -123,11 +123,11 @@ typedef struct sph_scene_desc {
     float cg_tol;                 /* relative residual of the implicit viscosity CG   */
     int32_t cg_max_iter;
     int32_t lanes_per_particle;   /* threads per fluid particle in the neighbour      */
-                                  /* sweeps: 1, 2 or 4 (they share the particle's     */
-                                  /* list); 0 = by size (4 up to 77,824 fluid         */
-                                  /* particles in the context, 2 up to twice that,    */
-                                  /* else 1).  A batch uses the largest value given   */
-                                  /* by its scenes.                                   */
+                                  /* sweeps: 1, 2, 4 or 8 (they share the particle's  */
+                                  /* list); 0 = by size (8 up to 38,912 fluid         */
+                                  /* particles in the context, 4 up to twice that, 2  */
+                                  /* up to four times, else 1).  A batch uses the     */
+                                  /* largest value given by its scenes.                                   */
     int32_t pressure_solver;      /* SPH_SOLVER_*                                     */
     float eos_stiffness;          /* WCSPH k, Pa (> 0)                                */
     float eos_exponent;           /* WCSPH gamma (>= 1; 0 = 7)                        */
@@ -257,8 +257,8 @@ sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
 
 /* Autotuning.  A scene created with cell_size < 0 lets sph_create choose its grid cell
  * size (h (1 + 2^-8), 27-cell stencil, or h/2 (1 + 2^-8), 125-cell stencil), the threads
- * per particle of the neighbour sweeps (1, 2 or 4; kept fixed when lanes_per_particle is
- * set) and, with one thread per particle, the number of neighbours each thread keeps in
+ * per particle of the neighbour sweeps (1, 2 or 4, or 8 instead of 2 for contexts small
+ * enough for 8; kept fixed when lanes_per_particle is set) and, with one thread per particle, the number of neighbours each thread keeps in
  * flight in the Jacobi passes (4 or 8) by timing a few CUDA-graph steps of every
  * candidate on temporary contexts, twice, keeping each candidate's faster time (the
  * default configuration is kept unless a candidate is more than 3 % faster); the choice

@@ -22,6 +22,15 @@ constexpr int kDefaultCapF = 96;
 constexpr int kDefaultCapB = 64;
 constexpr int64_t kAutoLaneThreads = 152 * 2048;  // resident threads of a full GB300
 
+// Threads per particle chosen by context size: the most (8, 4, 2, 1) whose threads still
+// fit the GPU's resident threads.
+int auto_lanes(int64_t nf)
+{
+    for (int l = 8; l > 1; l /= 2)
+        if (nf * l <= kAutoLaneThreads) return l;
+    return 1;
+}
+
 // PCISPH stiffness of a prototype particle with a full neighbourhood on the lattice of
 // spacing 2r (the predictive-corrective solver's constant): delta dt^2 = 1 / (2 (m/rho0)^2
 // (|sum grad W|^2 + sum |grad W|^2)), the cubic spline's gradient dW/dr = 48/(pi h^4) g(q),
@@ -189,8 +198,8 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
     if (d.max_fluid_neighbors < 0 || d.max_fluid_neighbors > 1024) return bad("max_fluid_neighbors");
     if (d.max_boundary_neighbors < 0 || d.max_boundary_neighbors > 1024) return bad("max_boundary_neighbors");
     if (d.lanes_per_particle != 0 && d.lanes_per_particle != 1 && d.lanes_per_particle != 2 &&
-        d.lanes_per_particle != 4)
-        return bad("lanes_per_particle (0, 1, 2 or 4)");
+        d.lanes_per_particle != 4 && d.lanes_per_particle != 8)
+        return bad("lanes_per_particle (0, 1, 2, 4 or 8)");
     if (!(d.warm_start_fraction >= 0.0f && d.warm_start_fraction <= 1.0f)) return bad("warm_start_fraction (0..1)");
     if (!(d.learned_fraction >= 0.0f && d.learned_fraction <= 1.0f)) return bad("learned_fraction (0..1)");
     if (d.rigid_coupling != SPH_COUPLING_WEAK && d.rigid_coupling != SPH_COUPLING_STRONG) return bad("rigid_coupling");
@@ -614,15 +623,14 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     int32_t nfblk = 0, nbblk = 0, ntblk = 0, nbodies = 0;
     int cap_f = 0, cap_b = 0;
     // threads per particle in the neighbour sweeps: one value for the whole context, the
-    // largest one given, else by size: enough threads to fill every SM (4 lanes below
-    // 152 x 2048 / 4 particles, 2 below twice that)
+    // largest one given, else by size: enough threads to fill every SM (8 lanes up to
+    // 152 x 2048 / 8 particles, 4 up to twice that, 2 up to four times)
     int lanes = 0;
     for (int s = 0; s < n; ++s) lanes = std::max(lanes, (int)descs[s].lanes_per_particle);
     if (lanes == 0) {
         int64_t nf = 0;
         for (int s = 0; s < n; ++s) nf += descs[s].n_fluid;
-        const int64_t fill = kAutoLaneThreads;
-        lanes = nf * 4 <= fill ? 4 : (nf * 2 <= fill ? 2 : 1);
+        lanes = auto_lanes(nf);
     }
     for (int s = 0; s < n; ++s) {
         const sph_scene_desc &d = descs[s];
@@ -1018,7 +1026,13 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
     };
     if (!cached) {
         const float factors[2] = {1.00390625f, 0.501953125f};
-        const int lanes_c[4] = {1, 1, 2, 4}, batch_c[4] = {4, 8, 4, 4};
+        int64_t nf_tot = 0;
+        for (int s = 0; s < n; ++s) nf_tot += descs[s].n_fluid;
+        // (lanes, batch) candidates; contexts small enough for 8 lanes try them instead of 2
+        // (unless the caller fixed the lanes: then only that count's candidates count)
+        int lanes_c[4] = {1, 1, 2, 4};
+        const int batch_c[4] = {4, 8, 4, 4};
+        if (fixed_lanes ? fixed_lanes == 8 : auto_lanes(nf_tot) == 8) lanes_c[2] = 8;
         best.n_trials = 0;
         for (int f = 0; f < 2; ++f)
             for (int b = 0; b < 4; ++b) {
@@ -1052,8 +1066,7 @@ sph_status create_tuned(const sph_scene_desc *descs, int32_t n, const sph_alloca
         // default is the one whose kernels are profiled
         int64_t nf_all = 0;
         for (int s = 0; s < n; ++s) nf_all += descs[s].n_fluid;
-        const int def_lanes = fixed_lanes ? fixed_lanes
-                                          : (nf_all * 4 <= kAutoLaneThreads ? 4 : (nf_all * 2 <= kAutoLaneThreads ? 2 : 1));
+        const int def_lanes = fixed_lanes ? fixed_lanes : auto_lanes(nf_all);
         for (int k = 0; k < best.n_trials; ++k)
             if (best.trial_cell_factor[k] == factors[0] && best.trial_batch[k] == 4 &&
                 best.trial_lanes[k] == def_lanes && best.trial_ms[k] <= 1.03f * best_ms) {

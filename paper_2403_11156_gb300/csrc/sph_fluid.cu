@@ -1,6 +1,6 @@
 // sph_fluid.cu -- per-particle sweeps of the DFSPH step.
 //
-// T threads (lanes, T = 1, 2 or 4) own one fluid particle in grid order.  The density
+// T threads (lanes, T = 1, 2, 4 or 8) own one fluid particle in grid order.  The density
 // sweep walks the (2R+1)^3-cell neighbourhood ((2R+1)^2 contiguous index ranges) once
 // per step and records the particle's neighbours in one k-major list, in candidate order
 // (with T > 1 the lanes test T consecutive candidates at a time and append the hits by a
@@ -799,6 +799,7 @@ void launch_pass_a(const Ptrs &P, int solver, int batch, cudaStream_t s)
 {
 #define SPH_A(S, B, T) k_pass_a<S, B, T><<<P.ntblk, kBlock, 0, s>>>(P)
     if (P.lanes == 4) { if (solver == 0) SPH_A(0, 4, 4); else SPH_A(1, 4, 4); }
+    else if (P.lanes == 8) { if (solver == 0) SPH_A(0, 4, 8); else SPH_A(1, 4, 8); }
     else if (P.lanes == 2) { if (solver == 0) SPH_A(0, 4, 2); else SPH_A(1, 4, 2); }
     else if (batch == 8) { if (solver == 0) SPH_A(0, 8, 1); else SPH_A(1, 8, 1); }
     else { if (solver == 0) SPH_A(0, 4, 1); else SPH_A(1, 4, 1); }
@@ -813,6 +814,7 @@ void launch_pass_b(const Ptrs &P, int solver, int warm, int batch, cudaStream_t 
         else { if (warm) SPH_B(1, 1, B, T); else SPH_B(1, 0, B, T); }             \
     } while (0)
     if (P.lanes == 4) SPH_BW(4, 4);
+    else if (P.lanes == 8) SPH_BW(4, 8);
     else if (P.lanes == 2) SPH_BW(4, 2);
     else if (batch == 8) SPH_BW(8, 1);
     else SPH_BW(4, 1);

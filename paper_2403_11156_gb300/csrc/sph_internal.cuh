@@ -222,7 +222,7 @@ struct Ptrs {
     const int32_t *tblk_scene;        // scene of each sweep block
     int32_t nfblk, nbblk, nscenes, nbodies_total;
     int32_t ntblk;                    // sweep blocks
-    int32_t lanes;                    // threads per fluid particle in the sweeps: 1, 2, 4
+    int32_t lanes;                    // threads per fluid particle in the sweeps: 1, 2, 4, 8
     int64_t NF, NB, NC;               // totals: fluid, boundary, cells
     // fluid
     float4 *pos_s, *vel_s, *pos_c, *vel_c;

@@ -139,6 +139,7 @@ __device__ __forceinline__ void for_range(const float4 *__restrict__ pos, uint32
 #define SPH_BY_LANES(P, CALL)                  \
     do {                                       \
         if ((P).lanes == 4) { CALL(4); }       \
+        else if ((P).lanes == 8) { CALL(8); }  \
         else if ((P).lanes == 2) { CALL(2); }  \
         else { CALL(1); }                      \
     } while (0)

@@ -7,7 +7,7 @@ column (250k-particle high-viscosity column), batch (64 dam breaks of 20k-200k p
 wcsph (the 8k dam break under the equation-of-state solver).
 --eager launches the kernels one by one (the form a kernel profiler can attribute);
 without it a step is one CUDA-graph launch.  --lanes sets the threads per particle of the
-neighbour sweeps (1, 2, 4; 0 chooses by size).  --surface / --image write the post-processing
+neighbour sweeps (1, 2, 4, 8; 0 chooses by size).  --surface / --image write the post-processing
 results of scene 0 after the steps: the iso-surface of the fluid (OBJ) and a shaded
 height map seen from above (PGM).  --warm picks the warm start of the solves (zero,
 previous, learned); the learned one loads a parameter block (--mlp, .npy) or, without one,

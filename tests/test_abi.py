@@ -46,7 +46,7 @@ def _bad(**kw):
     dict(radius=0.0), dict(rest_density=-1.0), dict(domain_max=(0.0, 0.2, 0.2)),
     dict(min_iter_density=-1), dict(max_iter_divergence=-3), dict(viscosity_mode=7), dict(warm_start=9),
     dict(dt_max=0.0), dict(max_fluid_neighbors=5000), dict(cell_size=0.01),
-    dict(lanes_per_particle=3), dict(lanes_per_particle=-1), dict(lanes_per_particle=8),
+    dict(lanes_per_particle=3), dict(lanes_per_particle=-1), dict(lanes_per_particle=16),
     dict(warm_start_fraction=1.5), dict(warm_start_fraction=-0.1), dict(learned_fraction=1.01),
     dict(learned_fraction=-1.0), dict(pressure_solver=3),
     dict(pressure_solver=1, eos_stiffness=0.0),
@@ -62,7 +62,7 @@ def test_rejects_bad_descriptors(lib, kw):
     assert e.value.status == sph.SPH_EINVAL
 
 
-@pytest.mark.parametrize("lanes", [0, 1, 2, 4])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
 def test_accepts_good_descriptors(lib, lanes):
     # without a GPU a valid scene passes validation and fails at the first CUDA call
     import torch

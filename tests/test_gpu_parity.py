@@ -2,7 +2,7 @@
 seeded inputs.
 
 Bit-exact: cell keys, (key, id) sort order, fluid and boundary neighbour counts.
-Every check runs with 1, 2 and 4 threads per particle in the neighbour sweeps (the
+Every check runs with 1, 2, 4 and 8 threads per particle in the neighbour sweeps (the
 neighbour sets are the same; only the FP32 summation order changes).
 FP32 vs FP64 fields from one step off identical states with the iteration counts forced
 equal: density, Psi and alpha within 1e-5 relative (alpha with a floor of 1e-3 rms for
@@ -35,7 +35,7 @@ def _small(**kw):
     return scenes.dam_break_small(seed=7, n=(9, 11, 13), box=0.4, **kw)
 
 
-LANES = [1, 2, 4]
+LANES = [1, 2, 4, 8]
 
 
 @pytest.mark.parametrize("lanes", LANES)

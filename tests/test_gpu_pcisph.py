@@ -23,7 +23,7 @@ def _small(**kw):
     return scenes.dam_break_pcisph(seed=7, n=(9, 11, 13), box=0.4, **kw)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_one_step_fields(lanes):
     d = forced(_small(lanes_per_particle=lanes), 0, 3)
     g = gpu_ctx(d)

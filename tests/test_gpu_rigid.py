@@ -39,7 +39,7 @@ def _submerged(lanes=1):
     return d
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_body_force_and_update(lanes):
     d = _submerged(lanes)
     dt = 5e-4

@@ -28,7 +28,7 @@ def test_noconverge_reported_and_state_advances():
     assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK   # already reported
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_overflow_reported(lanes):
     g = gpu_ctx(_small(max_fluid_neighbors=8, lanes_per_particle=lanes))
     g.sph_step(DT)
@@ -37,7 +37,9 @@ def test_overflow_reported(lanes):
 
 
 def test_lanes_default_by_size():
-    assert gpu_ctx(_small()).sph_get_tuning()["lanes"] == 4            # 1,287 particles
+    assert gpu_ctx(_small()).sph_get_tuning()["lanes"] == 8            # 1,287 particles
+    mid = scenes.dam_break_small(n=(40, 40, 30), box=1.0)               # 48,000
+    assert gpu_ctx(mid).sph_get_tuning()["lanes"] == 4
     big = scenes.dam_break_small(n=(60, 40, 40), box=1.4)               # 96,000
     assert gpu_ctx(big).sph_get_tuning()["lanes"] == 2
     assert gpu_ctx(dict(big, lanes_per_particle=1)).sph_get_tuning()["lanes"] == 1

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 DT = 4e-4
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("lanes", [1, 4, 8])
 def test_one_step_parity(lanes):
     d = forced(scenes.body_in_fluid(rigid_coupling=1, density=200.0, lanes_per_particle=lanes), 2, 3)
     g = gpu_ctx(d)

@@ -2,7 +2,8 @@
 (key, id) order and the neighbour counts stay bit-exact against the oracle's contracts
 (the oracle's key function takes the cell size as a parameter), density and alpha stay
 within 1e-5; autotuning times eight candidates (two cell sizes times (threads per
-particle, gather batch) in (1, 4), (1, 8), (2, 4), (4, 4)), keeps the fastest (or the
+particle, gather batch) in (1, 4), (1, 8), (2, 4), (4, 4), with (8, 4) instead of (2, 4) for
+contexts small enough for 8 lanes), keeps the fastest (or the
 default configuration when it is within 3 % of the fastest) and caches it;
 lanes_per_particle given by the caller stays fixed."""
 import numpy as np
@@ -42,7 +43,8 @@ def test_autotune_picks_fastest_and_caches():
     g = gpu_ctx(d, autotune=True)
     t = g.sph_get_tuning()
     assert t["tuned"] == 1 and t["from_cache"] == 0 and len(t["trials"]) == 8
-    assert sorted({(r["lanes"], r["gather_batch"]) for r in t["trials"]}) == [(1, 4), (1, 8), (2, 4), (4, 4)]
+    # 8,000 particles: small enough for 8 lanes, which replace 2 among the candidates
+    assert sorted({(r["lanes"], r["gather_batch"]) for r in t["trials"]}) == [(1, 4), (1, 8), (4, 4), (8, 4)]
     best = min(t["trials"], key=lambda r: r["ms_per_step"])
     chosen = [r for r in t["trials"] if (r["lanes"], r["gather_batch"]) == (t["lanes"], t["gather_batch"])
               and r["cell_factor"] == pytest.approx(t["cell_factor"])]
@@ -59,8 +61,9 @@ def test_autotune_picks_fastest_and_caches():
     assert t2["from_cache"] == 1 and t2["gather_batch"] == t["gather_batch"] and t2["lanes"] == t["lanes"]
 
 
-def test_autotune_keeps_given_lanes():
-    d = scenes.dam_break_small(seed=10, n=(12, 10, 10), lanes_per_particle=2)
+@pytest.mark.parametrize("lanes", [2, 8])
+def test_autotune_keeps_given_lanes(lanes):
+    d = scenes.dam_break_small(seed=10, n=(12, 10, 10), lanes_per_particle=lanes)
     t = gpu_ctx(d, autotune=True).sph_get_tuning()
-    assert t["lanes"] == 2 and len(t["trials"]) == 2
-    assert all(r["lanes"] == 2 for r in t["trials"])
+    assert t["lanes"] == lanes and len(t["trials"]) == 2
+    assert all(r["lanes"] == lanes for r in t["trials"])

@@ -21,7 +21,7 @@ def _column(**kw):
     return scenes.viscous_column(**base)
 
 
-@pytest.mark.parametrize("tol,lanes", [(1e-4, 1), (1e-6, 1), (1e-6, 2), (1e-6, 4)])
+@pytest.mark.parametrize("tol,lanes", [(1e-4, 1), (1e-6, 1), (1e-6, 2), (1e-6, 4), (1e-6, 8)])
 def test_cg_solves_oracle_system(tol, lanes):
     d = _column(cg_tol=tol, cg_max_iter=1000, lanes_per_particle=lanes)
     rng = np.random.default_rng(1)

@@ -22,7 +22,7 @@ def _small(**kw):
     return scenes.dam_break_wcsph(seed=7, n=(9, 11, 13), box=0.4, **kw)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 @pytest.mark.parametrize("visc", [0, 1])
 def test_one_step_fields(lanes, visc):
     d = _small(lanes_per_particle=lanes, viscosity_mode=visc)
