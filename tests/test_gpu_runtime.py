@@ -45,10 +45,11 @@ def test_lanes_default_by_size():
     assert gpu_ctx(dict(big, lanes_per_particle=1)).sph_get_tuning()["lanes"] == 1
 
 
-def test_lanes_change_only_rounding():
-    # the same 10 steps with 1 and 4 threads per particle: identical neighbour counts,
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_lanes_change_only_rounding(lanes):
+    # the same 10 steps with 1 and 4 (8) threads per particle: identical neighbour counts,
     # iteration counts equal or off by one, positions within FP32 rounding growth
-    a, b = gpu_ctx(_small(lanes_per_particle=1)), gpu_ctx(_small(lanes_per_particle=4))
+    a, b = gpu_ctx(_small(lanes_per_particle=1)), gpu_ctx(_small(lanes_per_particle=lanes))
     for g in (a, b):
         g.sph_steps(10, DT)
     np.testing.assert_array_equal(a.sph_read_field(sph.FIELD_NN_FLUID), b.sph_read_field(sph.FIELD_NN_FLUID))
