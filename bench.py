@@ -52,7 +52,7 @@ BOUNDARY_BYTES = 16                             # x_b, Psi_b per boundary partic
 # DRAM bytes (read + write) per launch measured by ncu on this workload at 1 thread per
 # particle, gather batch 4 and cell size h (1 + 2^-8), for the kernels as they are built
 # now (the roofline's `traffic`; null for any other kernel or configuration).
-TRAFFIC = {("dens_pass_a", 1, 4, 27): 211.56e6 + 16.48e6}
+TRAFFIC = {("dens_pass_a", 1, 4, 27): 211.56e6 + 16.68e6}
 # FP32 operations per neighbour pair in the list sweeps (distance, spline gradient, dot)
 FLOPS_PER_PAIR = {"dens_pass_a": 26, "div_pass_a": 24, "dens_pass_b": 22, "div_pass_b": 22,
                   "dens_warm_pass_b": 22, "div_warm_pass_b": 22, "nonpressure": 30,
