@@ -96,6 +96,7 @@ def lib():
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_set_mlp.argtypes = [C.c_void_p, dp]
         L.or_set_state.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        L.or_set_bodies.argtypes = [C.c_void_p, dp]
         L.or_step.argtypes = [C.c_void_p, C.c_double]
         L.or_field_width.restype = C.c_int64
         L.or_field_width.argtypes = [C.c_int32]
@@ -313,6 +314,14 @@ class Scene:
             return _p(a, C.c_double)
         lib().or_set_state(self.ptr, arr(x, 3 * self.nf), arr(v, 3 * self.nf),
                            arr(kappa_prev, self.nf), arr(kappa_v_prev, self.nf))
+
+    def set_bodies(self, bodies):
+        """Rigid state from rows of bodies()'s layout (com, quat, vel, omega; the force and
+        torque columns are ignored)."""
+        b = np.ascontiguousarray(bodies, dtype=np.float64).reshape(-1, 19)
+        assert len(b) == self.nbody
+        self._keep.append(b)
+        lib().or_set_bodies(self.ptr, _p(b, C.c_double))
 
     def set_mlp(self, params):
         params = np.ascontiguousarray(params, dtype=np.float64)

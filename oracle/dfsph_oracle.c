@@ -1256,6 +1256,21 @@ void or_get_bodies(const or_ctx *c, double *out)
     }
 }
 
+/* Rigid state in (test set-up: resuming from another implementation's state): per body    */
+/* com[3], quat[4], vel[3], omega[3] in the layout of or_get_bodies (its force and torque   */
+/* columns are ignored); the bodies' boundary particles are placed at the new pose.         */
+void or_set_bodies(or_ctx *c, const double *in)
+{
+    for (int32_t k = 0; k < c->nbody; ++k) {
+        or_body *B = &c->bodies[k];
+        const double *o = in + 19 * k;
+        for (int a = 0; a < 3; ++a) { B->com[a] = o[a]; B->vel[a] = o[7 + a]; B->omega[a] = o[10 + a]; }
+        for (int a = 0; a < 4; ++a) B->quat[a] = o[3 + a];
+    }
+    if (c->nbody > 0) set_boundary_from_bodies(c);
+    c->dt_next = cfl_dt(c);
+}
+
 double or_mass(const or_ctx *c) { return c->m; }
 double or_dt_next(const or_ctx *c) { return c->dt_next; }
 

@@ -4,7 +4,10 @@ contracts, neighbour counts bit-exact on a sample against brute force over all
 particles, density / alpha / Psi of every particle against the oracle (prepared on the
 full scene), one solver step's fields of every particle against the oracle (counts forced
 equal, the tolerances of the small-scene parity tests), the learned warm start's kappa0 of
-every particle against the oracle's FP64 network, and solver invariants over 20 steps."""
+every particle against the oracle's FP64 network, and solver invariants over 20 steps.  The
+64-scene batch (5.07M particles in one context) and the 250k-particle implicit-viscosity
+column are checked in their benchmark configurations too: the batch's smallest and largest
+scenes field by field, the column's CG velocity against the oracle's FP64 system."""
 import numpy as np
 import pytest
 
@@ -154,3 +157,120 @@ def test_learned_kappa0_full():
     assert both.sum() > 10_000
     # BF16 layers: normwise 3e-2 of the FP64 network's kappa0
     assert np.linalg.norm(kg[both] - ko[both]) <= 3e-2 * np.linalg.norm(ko[both])
+
+
+def test_batch_fields_full():
+    # the 64-scene batch in one context (the bench's batched configuration): the smallest and
+    # the largest scene against the oracle on its own, after the first step's sweep --
+    # keys, order and neighbour counts bit-exact, density and alpha within 1e-5
+    ds = scenes.batch_dam_break()
+    g = gpu_ctx(ds)
+    g.sph_step(0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    sizes = [len(d["fluid_x"]) for d in ds]
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        d = ds[k]
+        keys = oracle.cell_keys(d["fluid_x"], d["domain_min"], d["domain_max"],
+                                oracle.default_cell_size(d["radius"]))
+        np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_CELL_KEY, k), keys)
+        np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_SORTED_ID, k), oracle.sort_order(keys))
+        o = oracle.Scene(d)
+        o.prepare()
+        np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_NN_FLUID, k), o.get(oracle.NN_F).astype(np.int32))
+        assert_rel(g.sph_read_field(sph.FIELD_RHO, k), o.get(oracle.RHO), 1e-5, what="rho scene %d" % k)
+        assert_rel(g.sph_read_field(sph.FIELD_ALPHA, k), o.get(oracle.ALPHA), 1e-5, what="alpha scene %d" % k)
+
+
+def test_viscous_column_cg_full():
+    # the 250k-particle column of the viscosity benchmark, 200 CFL steps in (after its
+    # impact on the plane), then one step with the pressure solves off so that the velocity
+    # is the implicit viscosity solve's v*: it solves the oracle's FP64 system
+    # (I - dt A) v* = v + dt g to the CG tolerance plus the FP32 operator floor, and agrees
+    # with the oracle's own CG solution
+    d = scenes.viscous_column()
+    g = gpu_ctx(d)
+    g.sph_steps(200, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    x, v, _, _ = g.sph_read_state()
+    d1 = dict(d, fluid_x=x, fluid_v=v, max_iter_density=0, min_iter_density=0, warm_start=0,
+              divergence_solve=0)
+    h = gpu_ctx(d1)
+    h.sph_step(DT)
+    assert h.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    st = h.sph_get_stats()
+    tol = d["cg_tol"]
+    assert st["cg_iters"] > 5 and st["cg_residual"] <= tol * 1.0001
+    v_gpu = h.sph_read_state()[1].astype(np.float64)
+    o = oracle.Scene(d1)
+    o.prepare()
+    b = v.astype(np.float64) + DT * np.array(d["gravity"])
+    res = o.visc_operator(DT, v_gpu) - b
+    assert np.linalg.norm(res) <= (tol + 1e-5) * np.linalg.norm(b)
+    o.step(DT)
+    assert np.abs(v_gpu - o.get(oracle.V)).max() <= 20 * (tol + 1e-5) * np.abs(b).max()
+
+
+def test_wcsph_step_full():
+    # the bench's WCSPH workload (the 1.2M dam break without boxes at its acoustic step):
+    # 20 steps build a compressed state, then one step from the GPU's state on both sides,
+    # with the tolerances of the small-scene WCSPH parity test
+    d = scenes.dam_break_rigid(n_boxes=0)
+    d.update(scenes.wcsph_parameters(98 * 2 * d["radius"], d["radius"]))
+    dt = d["dt_max"]
+    g = gpu_ctx(d)
+    g.sph_steps(20, dt)
+    x, v, _, _ = g.sph_read_state()
+    o = oracle.Scene(d)
+    o.set_state(x, v, np.zeros(len(x), np.float32), np.zeros(len(x), np.float32))
+    g.sph_step(dt)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    o.step(dt)
+    k, gamma = d["eos_stiffness"], d["eos_exponent"]
+    assert_rel(g.sph_read_field(sph.FIELD_RHO), o.get(oracle.RHO), 1e-5, what="rho")
+    x2, v2, _, p2 = g.sph_read_state()
+    p_ref = o.get(oracle.PRESSURE)
+    assert p_ref.max() > 0
+    assert np.abs(p2 - p_ref).max() <= 1e-5 * gamma * k + 1e-5 * np.abs(p_ref).max()
+    dv = o.get(oracle.V) - o.get(oracle.V_NONP)
+    tol = 1e-3 * np.abs(dv).max() + 1e-5 * np.abs(o.get(oracle.V)).max()
+    assert np.abs(v2 - o.get(oracle.V)).max() <= tol
+    assert np.abs(x2 - o.get(oracle.X)).max() <= tol * dt + 1e-6
+
+
+def test_strong_coupling_step_full():
+    # the bench's strongly coupled 1.2M dam break (zero warm start, so that no warm-start gate
+    # decides apart between FP32 and FP64), 500 CFL steps in, with the boxes in the flow: the
+    # oracle resumes from the GPU's fluid and rigid state and takes the GPU's next step at the
+    # GPU's iteration counts.  Each body's force within 2e-4 of its magnitude (as in the
+    # small-scene strong test); torque and velocities within what that force error implies:
+    # the lever arm (the cube's half-diagonal) times it for the torque, dt / mass and
+    # dt r / I for the linear and angular velocity (the torque sums r x f over the surface
+    # and cancels, so its own magnitude is not the scale).  Fluid velocities within the
+    # DFSPH velocity bound of the full-size field test.
+    d = scenes.dam_break_rigid(rigid_coupling=scenes.COUPLING_STRONG, warm_start=scenes.WARM_ZERO)
+    g = gpu_ctx(d)
+    g.sph_steps(500, 0.0)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    x, v, _, _ = g.sph_read_state()
+    b0 = g.sph_read_bodies()
+    g.sph_step(DT)
+    assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+    st = g.sph_get_stats()
+    o = oracle.Scene(forced(d, int(st["div_iters"]), int(st["dens_iters"])))
+    o.set_state(x, v)
+    o.set_bodies(b0)
+    o.step(DT)
+    gb, ob = g.sph_read_bodies(), o.bodies()
+    for k, body in enumerate(d["bodies"]):
+        F, T = ob[k, 13:16], ob[k, 16:19]
+        assert np.abs(F).max() > 0                      # the box is in the fluid
+        f_tol = 2e-4 * np.abs(F).max()
+        edge = np.sqrt(6.0 * body["inertia"][0] / body["mass"])   # solid cube: I = m e^2 / 6
+        arm = 0.5 * np.sqrt(3.0) * edge
+        np.testing.assert_allclose(gb[k, 13:16], F, rtol=0, atol=f_tol)
+        np.testing.assert_allclose(gb[k, 16:19], T, rtol=0, atol=arm * f_tol)
+        np.testing.assert_allclose(gb[k, 7:10], ob[k, 7:10], rtol=0, atol=DT * f_tol / body["mass"] + 1e-9)
+        np.testing.assert_allclose(gb[k, 10:13], ob[k, 10:13], rtol=0,
+                                   atol=DT * arm * f_tol / body["inertia"][0] + 1e-9)
+    _, v_tol = field_tolerances(o, d, DT)
+    assert_abs(g.sph_read_state()[1], o.get(oracle.V), v_tol, "v")

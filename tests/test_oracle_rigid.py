@@ -70,3 +70,23 @@ def test_fluid_body_momentum_conserved(oracle_lib):
         pb = M * s.bodies()[0, 7:10]
         assert np.abs(pb).max() > 1e-6
         np.testing.assert_allclose(pf + pb, 0.0, atol=1e-10 * np.abs(pb).max())
+
+
+def test_resume_from_state_and_bodies(oracle_lib):
+    # a scene given another run's fluid state and rigid state continues exactly as that run
+    # does: the setters copy state and place the body's boundary particles at its pose
+    d = scenes.body_in_fluid(gravity=(0.0, 0.0, -9.81), warm_start=scenes.WARM_ZERO)
+    dt = 4e-4
+    a = oracle_lib.Scene(d)
+    for _ in range(3):
+        a.step(dt)
+    assert np.abs(a.bodies()[0, 7:13]).max() > 0          # the body moves
+    b = oracle_lib.Scene(d)
+    b.set_state(a.get(oracle_lib.X), a.get(oracle_lib.V))
+    b.set_bodies(a.bodies())
+    np.testing.assert_array_equal(b.get(oracle_lib.XB), a.get(oracle_lib.XB))
+    a.step(dt)
+    b.step(dt)
+    np.testing.assert_array_equal(b.get(oracle_lib.X), a.get(oracle_lib.X))
+    np.testing.assert_array_equal(b.get(oracle_lib.V), a.get(oracle_lib.V))
+    np.testing.assert_array_equal(b.bodies(), a.bodies())
