@@ -458,7 +458,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         run(c, b, "bsort_scan", [&] { launch_scan_cells(P, SORT_BOUNDARY, b); });
         run(c, b, "bsort_scatter", [&] { launch_scatter(P, SORT_BOUNDARY, b); });
         run(c, b, "bsort_rank_gather", [&] { launch_rank_gather(P, SORT_BOUNDARY, b); });
-        run(c, b, "boundary_psi", [&] { launch_boundary_psi(P, 1, b); });
+        run(c, b, "boundary_psi", [&] { launch_boundary_psi(P, b); });
         CK(cudaEventRecord(c->join, b));
     }
     run(c, s, "sort_key_hist", [&] { launch_key_hist(P, SORT_FLUID, s); });
@@ -510,7 +510,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
         return device_loop([&](cudaStream_t q, cudaGraphConditionalHandle h, int use) {
             run(c, q, na, [&] { launch_pass_a(P, solver, c->batch, q); });
             run(c, q, nb, [&] { launch_pass_b(P, solver, 0, c->batch, q); });
-            if (c->any_strong) run(c, q, "strong_coupling", [&] { launch_strong_update(P, q); });
+            if (c->any_strong) run(c, q, "strong_coupling", [&] { launch_strong_update(P, solver, q); });
             run(c, q, nc, [&] { launch_solver_check(P, solver, h, use, q); });
         });
     };
@@ -519,7 +519,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     if (c->any_div) {
         if (c->any_warm_div) {
             run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, s); });
-            if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
+            if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, -1, s); });
         }
         if ((st = loop(0)) != SPH_OK) return st;
     }
@@ -543,7 +543,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     // (written by the non-pressure kernel), applied once
     if (c->any_warm || c->any_wcsph) {
         run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, s); });
-        if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, s); });
+        if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, -1, s); });
     }
     if ((st = loop(1)) != SPH_OK) return st;
     if (c->any_bodies) {
@@ -937,7 +937,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         launch_scan_cells(P, SORT_BOUNDARY, s);
         launch_scatter(P, SORT_BOUNDARY, s);
         launch_rank_gather(P, SORT_BOUNDARY, s);
-        launch_boundary_psi(P, 0, s);
+        launch_boundary_psi(P, s);
         sph_status cs = check_async(c);
         if (cs != SPH_OK) return bail(cs);
     }

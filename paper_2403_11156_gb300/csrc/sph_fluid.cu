@@ -44,14 +44,6 @@ __device__ __forceinline__ BlockCtx fluid_ctx(const Ptrs &P)
     return c;
 }
 
-__device__ __forceinline__ bool solver_active(const SceneDev &sc, const SceneState &st, int s)
-{
-    if (s == 0 && !sc.div_on) return false;
-    int it = st.it[s];
-    if (it >= sc.max_it[s]) return false;
-    return it < sc.min_it[s] || st.err[s] > (double)sc.eta[s];
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {

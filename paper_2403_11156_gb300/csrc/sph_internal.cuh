@@ -272,6 +272,17 @@ __device__ __forceinline__ int32_t cell_coord(float x, float o, float c, int32_t
 }
 
 // Neighbour predicate contract: d2 = ((dx*dx)+(dy*dy))+(dz*dz) in float, no FMA, d2 < h2.
+// Whether a scene's Jacobi solve s (0 divergence, 1 density) takes another iteration: its
+// pass A and B run, and so does the strong-coupling body update after them, exactly when
+// this holds (the state only changes in the check kernel that ends the iteration).
+__device__ __forceinline__ bool solver_active(const SceneDev &sc, const SceneState &st, int s)
+{
+    if (s == 0 && !sc.div_on) return false;
+    int it = st.it[s];
+    if (it >= sc.max_it[s]) return false;
+    return it < sc.min_it[s] || st.err[s] > (double)sc.eta[s];
+}
+
 __device__ __forceinline__ float pred_d2(float4 a, float4 b, float &dx, float &dy, float &dz)
 {
     dx = __fsub_rn(a.x, b.x);
@@ -322,10 +333,13 @@ cudaError_t post_height_map(const float4 *pos, int64_t n, const float lo[2], con
 
 // ------------------------------------------------------------------ rigid (sph_rigid.cu)
 void launch_boundary_update(const Ptrs &P, cudaStream_t s);
-void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s);
+void launch_boundary_psi(const Ptrs &P, cudaStream_t s);
 void launch_body_force(const Ptrs &P, cudaStream_t s);
 void launch_body_reduce(const Ptrs &P, cudaStream_t s);
 void launch_body_touch(const Ptrs &P, cudaStream_t s);
-void launch_strong_update(const Ptrs &P, cudaStream_t s);
+// Strong coupling: the body update from the stiffness just applied.  solver = 0 or 1 inside
+// that solver's Jacobi loop (scenes whose solve is no longer active skip it), -1 after a
+// warm-start pass.
+void launch_strong_update(const Ptrs &P, int solver, cudaStream_t s);
 
 }  // namespace sph

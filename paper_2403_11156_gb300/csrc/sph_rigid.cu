@@ -37,12 +37,13 @@ __global__ void __launch_bounds__(kBlock) k_boundary_update(Ptrs P)
                             (float)(B.vel[2] + (B.omega[0] * wy - B.omega[1] * wx)), 0.0f);
 }
 
-// Psi_b = rho0 / (sigma (1 + sum_k w(q_bk)))  (grid order; stored in bpos_s.w)
-__global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P, int only_moving)
+// Psi_b = rho0 / (sigma (1 + sum_k w(q_bk)))  (grid order; stored in bpos_s.w).  Every
+// scene's: a per-step boundary sort (any moving body in the context) rebuilds the grid
+// order, and with it the w slot, of every scene's boundary, static walls included.
+__global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P)
 {
     kernel_enter(P.ctl, KID_PSI);
     const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
-    if (only_moving && !sc.has_moving) return;
     int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
     if (local >= sc.nb) return;
     int64_t b = sc.b_off + local;
@@ -94,13 +95,15 @@ __device__ double block_sum_d(double v, double *sh)
 // INC = true: strongly coupled scenes, from the stiffness just applied (kappa/rho of the
 // current sweep).
 template <int T, bool INC>
-__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P)
+__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int solver)
 {
     __shared__ double sh[kBlock / 32];
     kernel_enter(P.ctl, INC ? KID_BFORCE_INC : KID_BFORCE);
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     if (sc.nbody == 0 || (sc.strong != 0) != INC) return;  // uniform per block
+    // inside a Jacobi loop of a batch, a scene whose solve has stopped applied no stiffness
+    if (INC && solver >= 0 && !solver_active(sc, *c.st, solver)) return;
     const int64_t i = c.i, NF = P.NF;
     const int nb = c.valid ? P.nnb[i] : 0;
     // which bodies this block's particles touch (most blocks touch none, or only walls).
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
 // Strong coupling: one block per body sums the partials of the stiffness just applied (in
 // block order), adds them to the step's force and torque and applies the impulse,
 // v += dt F / M, omega += dt I^-1 tau (world inertia of the step's orientation).
-__global__ void __launch_bounds__(256) k_body_apply(Ptrs P)
+__global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int solver)
 {
     __shared__ double sh[8];
     __shared__ double s_f[6];
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P)
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];
     if (!sc.strong) return;
+    if (solver >= 0 && !solver_active(sc, P.st[B.scene], solver)) return;   // as k_body_force
     // the partials of the blocks that touch this body, in block order (thread t takes
     // blocks t, t + 256, ...; the other blocks contribute nothing)
     const int k = body - sc.body_off;
@@ -299,13 +303,13 @@ void launch_body_touch(const Ptrs &P, cudaStream_t s)
 #undef SPH_L
 }
 
-void launch_strong_update(const Ptrs &P, cudaStream_t s)
+void launch_strong_update(const Ptrs &P, int solver, cudaStream_t s)
 {
     if (!P.ntblk || !P.nbodies_total) return;
-#define SPH_L(T) k_body_force<T, true><<<P.ntblk, kBlock, 0, s>>>(P)
+#define SPH_L(T) k_body_force<T, true><<<P.ntblk, kBlock, 0, s>>>(P, solver)
     SPH_BY_LANES(P, SPH_L);
 #undef SPH_L
-    k_body_apply<<<P.nbodies_total, 256, 0, s>>>(P);
+    k_body_apply<<<P.nbodies_total, 256, 0, s>>>(P, solver);
     if (P.nbblk) k_boundary_vel<<<P.nbblk, kBlock, 0, s>>>(P);
 }
 
@@ -313,14 +317,14 @@ void launch_boundary_update(const Ptrs &P, cudaStream_t s)
 {
     if (P.nbblk) k_boundary_update<<<P.nbblk, kBlock, 0, s>>>(P);
 }
-void launch_boundary_psi(const Ptrs &P, int only_moving, cudaStream_t s)
+void launch_boundary_psi(const Ptrs &P, cudaStream_t s)
 {
-    if (P.nbblk) k_boundary_psi<<<P.nbblk, kBlock, 0, s>>>(P, only_moving);
+    if (P.nbblk) k_boundary_psi<<<P.nbblk, kBlock, 0, s>>>(P);
 }
 void launch_body_force(const Ptrs &P, cudaStream_t s)
 {
     if (!P.ntblk) return;
-#define SPH_L(T) k_body_force<T, false><<<P.ntblk, kBlock, 0, s>>>(P)
+#define SPH_L(T) k_body_force<T, false><<<P.ntblk, kBlock, 0, s>>>(P, -1)
     SPH_BY_LANES(P, SPH_L);
 #undef SPH_L
 }
