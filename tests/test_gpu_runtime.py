@@ -181,3 +181,34 @@ def test_large_batch_equals_single():
         assert sb["total_dens_iters"] == ss["total_dens_iters"]
         assert sb["total_div_iters"] == ss["total_div_iters"]
         assert sb["cg_iters"] == ss["cg_iters"]
+
+
+def test_every_kind_batched_matches_single():
+    # one context holding a scene of every kind: DFSPH, PCISPH, WCSPH, a strongly coupled
+    # body (moving boundary), an implicit-viscosity column, and a DFSPH scene without the
+    # divergence solve or warm start and with XSPH.  Every kernel a kind needs runs over the
+    # whole batch and must leave the other kinds untouched: each scene steps bit-identically
+    # to itself alone (one thread per particle everywhere, so the summation orders match)
+    one = dict(lanes_per_particle=1)
+    ds = [scenes.dam_break_small(seed=4, n=(9, 11, 13), box=0.4, **one),
+          scenes.dam_break_pcisph(seed=7, n=(9, 11, 13), box=0.4, **one),
+          scenes.dam_break_wcsph(seed=7, n=(9, 11, 13), box=0.4, **one),
+          scenes.body_in_fluid(rigid_coupling=1, density=200.0, **one),
+          scenes.viscous_column(n=(8, 8, 16), plane_size=0.15, **one),
+          scenes.dam_break_small(seed=6, n=(7, 9, 8), box=0.3, divergence_solve=0, warm_start=0,
+                                 viscosity_mode=2, xsph_c=0.1, **one)]
+    dt = 2e-4
+    done = (sph.SPH_OK, sph.SPH_ENOCONVERGE)
+    batch = gpu_ctx(ds)
+    batch.sph_steps(5, dt)
+    assert batch.sph_synchronize(raise_on_error=False) in done
+    for k, d in enumerate(ds):
+        single = gpu_ctx(d)
+        single.sph_steps(5, dt)
+        assert single.sph_synchronize(raise_on_error=False) in done
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w, err_msg="scene %d" % k)
+        np.testing.assert_array_equal(batch.sph_read_bodies(k), single.sph_read_bodies())
+        bs, ss = batch.sph_get_stats(k), single.sph_get_stats()
+        for key in ("total_dens_iters", "total_div_iters", "cg_iters"):
+            assert bs[key] == ss[key], (k, key)
