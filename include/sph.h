@@ -249,6 +249,16 @@ sph_status sph_get_stats(sph_ctx *ctx, int32_t scene, sph_stats *out);
  * force[3], torque[3] (fluid pressure force and torque of the last step). */
 sph_status sph_read_bodies(sph_ctx *ctx, int32_t scene, double *out);
 
+/* Rigid state into one scene (checkpoint resume, with sph_write_state for the fluid): per
+ * body the first 13 doubles of the sph_read_bodies layout, com[3], quat[4], vel[3],
+ * omega[3]. The force and torque columns are ignored, so a sph_read_bodies buffer can be
+ * passed back as it is. Values are stored as given (the integrator renormalises the
+ * quaternion every step); the body's boundary particles take the new pose at the next
+ * step start, where they are placed from it anyway. Host buffer, caller-owned, read during
+ * the call; synchronises. SPH_EINVAL for a bad scene index, a NULL buffer with bodies in
+ * the scene, a non-finite value or a quaternion of zero norm (nothing is written then). */
+sph_status sph_write_bodies(sph_ctx *ctx, int32_t scene, const double *in);
+
 /* Execution mode: graph != 0 replays the step as one CUDA graph with device-side loop
  * control (default); 0 launches kernels one by one with host-side loop control.
  * timing != 0 (eager mode only) brackets every kernel with CUDA events on the context

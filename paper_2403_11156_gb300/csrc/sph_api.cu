@@ -1410,6 +1410,37 @@ sph_status sph_read_bodies(sph_ctx *c, int32_t scene, double *out)
     return SPH_OK;
 }
 
+sph_status sph_write_bodies(sph_ctx *c, int32_t scene, const double *in)
+{
+    sph_status st = scene_ok(c, scene);
+    if (st != SPH_OK) return st;
+    const SceneDev &q = c->scenes[scene];
+    if (q.nbody == 0) return SPH_OK;
+    if (!in) return fail(c, SPH_EINVAL, "sph_write_bodies: NULL buffer");
+    for (int k = 0; k < q.nbody; ++k) {
+        const double *o = in + 19 * k;
+        double n2 = 0.0;
+        for (int a = 0; a < 13; ++a)
+            if (!std::isfinite(o[a])) return fail(c, SPH_EINVAL, "sph_write_bodies: body %d not finite", k);
+        for (int a = 0; a < 4; ++a) n2 += o[3 + a] * o[3 + a];
+        if (!(n2 > 0.0)) return fail(c, SPH_EINVAL, "sph_write_bodies: body %d has a zero quaternion", k);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<BodyDev> hb(q.nbody);
+    CK(cudaMemcpy(hb.data(), c->P.bodies + q.body_off, sizeof(BodyDev) * q.nbody, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < q.nbody; ++k) {
+        const double *o = in + 19 * k;
+        for (int a = 0; a < 3; ++a) {
+            hb[k].com[a] = o[a];
+            hb[k].vel[a] = o[7 + a];
+            hb[k].omega[a] = o[10 + a];
+        }
+        for (int a = 0; a < 4; ++a) hb[k].quat[a] = o[3 + a];
+    }
+    CK(cudaMemcpy(c->P.bodies + q.body_off, hb.data(), sizeof(BodyDev) * q.nbody, cudaMemcpyHostToDevice));
+    return SPH_OK;
+}
+
 sph_status sph_set_mode(sph_ctx *c, int32_t graph, int32_t timing)
 {
     sph_status st = check_ctx(c);

@@ -149,6 +149,7 @@ def load():
     L.sph_read_field.argtypes = [vp, ip, ip, vp, ip]
     L.sph_get_stats.argtypes = [vp, ip, C.POINTER(Stats)]
     L.sph_read_bodies.argtypes = [vp, ip, dp]
+    L.sph_write_bodies.argtypes = [vp, ip, dp]
     L.sph_set_mode.argtypes = [vp, ip, ip]
     L.sph_kernel_times.argtypes = [vp, C.POINTER(KernelTime), ip, C.POINTER(C.c_int32), ip]
     L.sph_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -383,6 +384,16 @@ class Context:
         _check(self.ctx, load().sph_read_bodies(self.ctx, scene,
                                                 out.ctypes.data_as(C.POINTER(C.c_double))))
         return out[:nb]
+
+    def sph_write_bodies(self, scene, bodies):
+        """Rigid state from rows of sph_read_bodies' layout (com, quat, vel, omega; the
+        force and torque columns are ignored)."""
+        nb = len(self.descs[scene].get("bodies", []))
+        b = np.ascontiguousarray(bodies, dtype=np.float64).reshape(-1, 19)
+        if len(b) != nb:
+            raise ValueError("scene %d has %d bodies, got %d rows" % (scene, nb, len(b)))
+        _check(self.ctx, load().sph_write_bodies(self.ctx, scene,
+                                                 b.ctypes.data_as(C.POINTER(C.c_double))))
 
     def sph_probe_wait_timeout(self, spin_limit=1000):
         """Enqueue a bounded wait that runs out (the device error path); returns the status

@@ -104,3 +104,32 @@ def test_batch_with_static_scene_matches_single():
             np.testing.assert_array_equal(u, w)
         np.testing.assert_array_equal(batch.sph_read_field(sph.FIELD_PSI, k), single.sph_read_field(sph.FIELD_PSI))
         np.testing.assert_array_equal(batch.sph_read_bodies(k), single.sph_read_bodies())
+
+
+def test_checkpoint_resume_with_bodies_bit_exact():
+    # fluid state, solver memory (sph_write_state) and rigid state (sph_write_bodies) taken
+    # from a run with the boxes in the fluid resume it exactly
+    d = _submerged()
+    a = gpu_ctx(d)
+    a.sph_steps(5, 4e-4)
+    a.sph_synchronize(raise_on_error=False)
+    x, v, _, _ = a.sph_read_state()
+    kp, kvp = a.sph_read_field(sph.FIELD_KAPPA_PREV), a.sph_read_field(sph.FIELD_KAPPA_V_PREV)
+    bodies = a.sph_read_bodies()
+    assert np.abs(bodies[:, 7:13]).max() > 0            # the boxes move
+    b = gpu_ctx(d)
+    b.sph_write_state(0, x, v, kp, kvp)
+    b.sph_write_bodies(0, bodies)
+    for g in (a, b):
+        g.sph_steps(3, 4e-4)
+        g.sph_synchronize(raise_on_error=False)
+    for u, w in zip(a.sph_read_state(), b.sph_read_state()):
+        np.testing.assert_array_equal(u, w)
+    np.testing.assert_array_equal(a.sph_read_bodies(), b.sph_read_bodies())
+    # malformed rigid state is refused and leaves the bodies as they were
+    before = b.sph_read_bodies()
+    for bad in (np.zeros_like(bodies), np.where(np.arange(19) == 0, np.nan, bodies)):
+        with pytest.raises(sph.SphError) as e:
+            b.sph_write_bodies(0, bad)
+        assert e.value.status == sph.SPH_EINVAL
+    np.testing.assert_array_equal(b.sph_read_bodies(), before)
