@@ -519,7 +519,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     if (c->any_div) {
         if (c->any_warm_div) {
             run(c, s, "div_warm_pass_b", [&] { launch_pass_b(P, 0, 1, c->batch, s); });
-            if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, -1, s); });
+            if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, 2, s); });
         }
         if ((st = loop(0)) != SPH_OK) return st;
     }
@@ -543,7 +543,7 @@ sph_status enqueue_step(sph_ctx *c, cudaStream_t s, bool capture)
     // (written by the non-pressure kernel), applied once
     if (c->any_warm || c->any_wcsph) {
         run(c, s, "dens_warm_pass_b", [&] { launch_pass_b(P, 1, 1, c->batch, s); });
-        if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, -1, s); });
+        if (c->any_strong) run(c, s, "strong_coupling", [&] { launch_strong_update(P, 3, s); });
     }
     if ((st = loop(1)) != SPH_OK) return st;
     if (c->any_bodies) {

@@ -428,8 +428,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P)
     // uniform per block; WCSPH scenes apply their equation-of-state pressure here.  In the
     // loop, a scene's pass B runs exactly when its pass A did: the solver state only
     // changes in the check kernel that follows.
-    const bool run = WARM ? ((sc.warm != 0 && (S == 1 || sc.div_on)) || (S == 1 && sc.solver == 1))
-                          : solver_active(sc, st, S);
+    const bool run = WARM ? warm_pass_runs(sc, S) : solver_active(sc, st, S);
     if (run) {
         const int64_t i = c.i, NF = P.NF;
         const int s = c.s;

@@ -283,6 +283,23 @@ __device__ __forceinline__ bool solver_active(const SceneDev &sc, const SceneSta
     return it < sc.min_it[s] || st.err[s] > (double)sc.eta[s];
 }
 
+// Whether a scene's warm-start pass of solve s applies a pressure: its warm start (the
+// divergence solve's only where that solve runs), or for a WCSPH scene the equation-of-state
+// pressure, which the density solve's warm pass applies once.
+__device__ __forceinline__ bool warm_pass_runs(const SceneDev &sc, int s)
+{
+    return (sc.warm != 0 && (s == 1 || sc.div_on)) || (s == 1 && sc.solver == 1);
+}
+
+// The strong-coupling body update applies where its scene's pass B just ran: phase s (0
+// divergence, 1 density) inside that solve's Jacobi loop, 2 + s after its warm-start pass
+// (a negative phase: unconditionally).
+__device__ __forceinline__ bool strong_update_applies(const SceneDev &sc, const SceneState &st, int phase)
+{
+    if (phase < 0) return true;
+    return phase >= 2 ? warm_pass_runs(sc, phase - 2) : solver_active(sc, st, phase);
+}
+
 __device__ __forceinline__ float pred_d2(float4 a, float4 b, float &dx, float &dy, float &dz)
 {
     dx = __fsub_rn(a.x, b.x);
@@ -337,9 +354,9 @@ void launch_boundary_psi(const Ptrs &P, cudaStream_t s);
 void launch_body_force(const Ptrs &P, cudaStream_t s);
 void launch_body_reduce(const Ptrs &P, cudaStream_t s);
 void launch_body_touch(const Ptrs &P, cudaStream_t s);
-// Strong coupling: the body update from the stiffness just applied.  solver = 0 or 1 inside
-// that solver's Jacobi loop (scenes whose solve is no longer active skip it), -1 after a
-// warm-start pass.
-void launch_strong_update(const Ptrs &P, int solver, cudaStream_t s);
+// Strong coupling: the body update from the stiffness just applied, in the scenes whose pass
+// B just ran (phase as for strong_update_applies: 0 or 1 in that solve's Jacobi loop, 2 + s
+// after solve s's warm-start pass).
+void launch_strong_update(const Ptrs &P, int phase, cudaStream_t s);
 
 }  // namespace sph

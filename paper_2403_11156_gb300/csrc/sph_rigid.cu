@@ -95,15 +95,17 @@ __device__ double block_sum_d(double v, double *sh)
 // INC = true: strongly coupled scenes, from the stiffness just applied (kappa/rho of the
 // current sweep).
 template <int T, bool INC>
-__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int solver)
+__global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int phase)
 {
     __shared__ double sh[kBlock / 32];
     kernel_enter(P.ctl, INC ? KID_BFORCE_INC : KID_BFORCE);
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
     if (sc.nbody == 0 || (sc.strong != 0) != INC) return;  // uniform per block
-    // inside a Jacobi loop of a batch, a scene whose solve has stopped applied no stiffness
-    if (INC && solver >= 0 && !solver_active(sc, *c.st, solver)) return;
+    // in a batch, a scene whose pass B did not run (its solve has stopped, or it has no warm
+    // start) applied no stiffness here: its bodies and their boundary velocities stay as they
+    // would alone
+    if (INC && !strong_update_applies(sc, *c.st, phase)) return;
     const int64_t i = c.i, NF = P.NF;
     const int nb = c.valid ? P.nnb[i] : 0;
     // which bodies this block's particles touch (most blocks touch none, or only walls).
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
 // Strong coupling: one block per body sums the partials of the stiffness just applied (in
 // block order), adds them to the step's force and torque and applies the impulse,
 // v += dt F / M, omega += dt I^-1 tau (world inertia of the step's orientation).
-__global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int solver)
+__global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int phase)
 {
     __shared__ double sh[8];
     __shared__ double s_f[6];
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int solver)
     BodyDev &B = P.bodies[body];
     const SceneDev &sc = P.scenes[B.scene];
     if (!sc.strong) return;
-    if (solver >= 0 && !solver_active(sc, P.st[B.scene], solver)) return;   // as k_body_force
+    if (!strong_update_applies(sc, P.st[B.scene], phase)) return;   // as k_body_force
     // the partials of the blocks that touch this body, in block order (thread t takes
     // blocks t, t + 256, ...; the other blocks contribute nothing)
     const int k = body - sc.body_off;
@@ -274,12 +276,17 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int solver)
 }
 
 // Strong coupling: the boundary particles of strongly coupled bodies follow the updated
-// body velocities, v_b = v + omega x (x_b - com) (grid order).
-__global__ void __launch_bounds__(kBlock) k_boundary_vel(Ptrs P)
+// body velocities, v_b = v + omega x (x_b - com) (grid order).  Only where the body update
+// applied: the step-start values come from the body-frame offsets, these from the float
+// boundary positions, and the two differ in the last bit, so a scene must see this kernel
+// exactly where it would alone.
+__global__ void __launch_bounds__(kBlock) k_boundary_vel(Ptrs P, int phase)
 {
     kernel_enter(P.ctl, KID_BVEL);
-    const SceneDev &sc = P.scenes[P.bblk_scene[blockIdx.x]];
+    const int32_t scene = P.bblk_scene[blockIdx.x];
+    const SceneDev &sc = P.scenes[scene];
     if (!sc.strong || sc.nbody == 0) return;
+    if (!strong_update_applies(sc, P.st[scene], phase)) return;
     const int64_t local = (int64_t)(blockIdx.x - sc.bblk_first) * kBlock + threadIdx.x;
     if (local >= sc.nb) return;
     const int64_t b = sc.b_off + local;
@@ -303,14 +310,14 @@ void launch_body_touch(const Ptrs &P, cudaStream_t s)
 #undef SPH_L
 }
 
-void launch_strong_update(const Ptrs &P, int solver, cudaStream_t s)
+void launch_strong_update(const Ptrs &P, int phase, cudaStream_t s)
 {
     if (!P.ntblk || !P.nbodies_total) return;
-#define SPH_L(T) k_body_force<T, true><<<P.ntblk, kBlock, 0, s>>>(P, solver)
+#define SPH_L(T) k_body_force<T, true><<<P.ntblk, kBlock, 0, s>>>(P, phase)
     SPH_BY_LANES(P, SPH_L);
 #undef SPH_L
-    k_body_apply<<<P.nbodies_total, 256, 0, s>>>(P, solver);
-    if (P.nbblk) k_boundary_vel<<<P.nbblk, kBlock, 0, s>>>(P);
+    k_body_apply<<<P.nbodies_total, 256, 0, s>>>(P, phase);
+    if (P.nbblk) k_boundary_vel<<<P.nbblk, kBlock, 0, s>>>(P, phase);
 }
 
 void launch_boundary_update(const Ptrs &P, cudaStream_t s)

@@ -89,3 +89,23 @@ def test_batch_with_longer_solve_matches_single():
         for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
             np.testing.assert_array_equal(u, w)
         np.testing.assert_array_equal(batch.sph_read_bodies(k), single.sph_read_bodies())
+
+
+def test_batch_with_warm_started_scene_matches_single():
+    # a strongly coupled scene without a warm start beside a scene with the previous-step
+    # warm start: the batch runs the warm-start passes, and their body update must leave
+    # the first scene's body alone (its warm pass applied nothing); both scenes step
+    # bit-identically to each alone
+    strong = scenes.body_in_fluid(rigid_coupling=1, density=200.0, warm_start=scenes.WARM_ZERO)
+    other = scenes.dam_break_small(seed=7, n=(9, 11, 13), box=0.4)
+    done = (sph.SPH_OK, sph.SPH_ENOCONVERGE)
+    batch = gpu_ctx([strong, other])
+    batch.sph_steps(4, DT)
+    assert batch.sph_synchronize(raise_on_error=False) in done
+    for k, d in enumerate((strong, other)):
+        single = gpu_ctx(d)
+        single.sph_steps(4, DT)
+        assert single.sph_synchronize(raise_on_error=False) in done
+        for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
+            np.testing.assert_array_equal(u, w)
+        np.testing.assert_array_equal(batch.sph_read_bodies(k), single.sph_read_bodies())
