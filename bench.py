@@ -572,6 +572,11 @@ def main():
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured" else "fallback 6.8 TB/s",
             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
             "share_of_step": k_ms / total_ms if total_ms else None}
+    if roof["traffic"]:
+        # the DRAM rate the launch actually sustains: ncu's bytes per launch (the algorithmic
+        # state plus the neighbour-list stream) over the live launch time
+        roof["traffic_gbs"] = roof["traffic"] / per_launch_s / 1e9
+        roof["traffic_frac"] = roof["traffic_gbs"] / hbm
     if name in FLOPS_PER_PAIR:
         # ALU view of the same kernel: counted FP32 flops over the measured mean neighbour count
         nn_mean = 33.0
