@@ -269,13 +269,13 @@ sph_status sph_set_mode(sph_ctx *ctx, int32_t graph, int32_t timing);
  * size (h (1 + 2^-8), 27-cell stencil, or h/2 (1 + 2^-8), 125-cell stencil), the threads
  * per particle of the neighbour sweeps (1, 2 or 4, or 8 instead of 2 for contexts small
  * enough for 8; kept fixed when lanes_per_particle is set) and, with one thread per
- * particle, the number of neighbours each thread keeps in flight in the Jacobi passes
- * (4 or 8) by timing a few CUDA-graph steps of every
- * candidate on temporary contexts, twice, keeping each candidate's faster time (the
- * default configuration is kept unless a candidate is more than 3 % faster); the choice
- * is cached per process for the same device and workload size (log2 of the fluid count,
- * scene count, bodies, viscosity mode, lanes_per_particle).  Neighbour sets do not
- * depend on the choice; the summation order, and so the last bits of FP32 results, may. */
+ * particle, the number of neighbours each thread keeps in flight in the Jacobi passes (4
+ * or 8) by timing a few CUDA-graph steps of every candidate on temporary contexts,
+ * twice, keeping each candidate's faster time (the default configuration is kept unless
+ * a candidate is more than 3 % faster); the choice is cached per process for the same
+ * device and workload size (log2 of the fluid count, scene count, bodies, viscosity
+ * mode, lanes_per_particle).  Neighbour sets do not depend on the choice; the summation
+ * order, and so the last bits of FP32 results, may. */
 typedef struct sph_tuning {
     int32_t tuned;            /* 1 if this context was autotuned                     */
     int32_t from_cache;       /* the choice came from the per-process cache          */
