@@ -212,3 +212,25 @@ def test_every_kind_batched_matches_single():
         bs, ss = batch.sph_get_stats(k), single.sph_get_stats()
         for key in ("total_dens_iters", "total_div_iters", "cg_iters"):
             assert bs[key] == ss[key], (k, key)
+
+
+def test_checkpoint_resume_inside_a_batch():
+    # the state of one scene of a batch (fluid, solver memory, bodies) written into the same
+    # scene of a fresh batch context resumes it exactly, and the other scenes are untouched
+    ds = [_small(seed=3, lanes_per_particle=1),
+          scenes.body_in_fluid(rigid_coupling=1, density=200.0, lanes_per_particle=1)]
+    a = gpu_ctx(ds)
+    a.sph_steps(4, DT)
+    a.sph_synchronize(raise_on_error=False)
+    b = gpu_ctx(ds)
+    x, v, _, _ = a.sph_read_state(1)
+    b.sph_write_state(1, x, v, a.sph_read_field(sph.FIELD_KAPPA_PREV, 1), a.sph_read_field(sph.FIELD_KAPPA_V_PREV, 1))
+    b.sph_write_bodies(1, a.sph_read_bodies(1))
+    x0 = b.sph_read_state(0)[0].copy()
+    np.testing.assert_array_equal(x0, ds[0]["fluid_x"])     # scene 0 still at its start
+    for g in (a, b):
+        g.sph_steps(2, DT)
+        g.sph_synchronize(raise_on_error=False)
+    for u, w in zip(a.sph_read_state(1), b.sph_read_state(1)):
+        np.testing.assert_array_equal(u, w)
+    np.testing.assert_array_equal(a.sph_read_bodies(1), b.sph_read_bodies(1))
