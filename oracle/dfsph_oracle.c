@@ -23,7 +23,8 @@
  * Pins (see tests/test_oracle_*.py): kernel normalisation and gradient antisymmetry,
  * lattice rest density, brute-force neighbour sets, momentum antisymmetry of pressure,
  * viscosity and boundary forces, hydrostatic pressure in a resting tank, operator
- * symmetry of implicit viscosity, MLP gradients against finite differences.
+ * symmetry of implicit viscosity, MLP gradients against finite differences, and a run
+ * resumed through the state setters (fluid and rigid) continuing bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
