@@ -5,8 +5,11 @@ import this package.  It loads ``liboracle.so`` (built from ``dfsph_oracle.c`` b
 :func:`build`) through ctypes and shares nothing with the CUDA library.
 
 Parity unpinned: the absolute multi-step trajectories (splash shapes) of the dam-break
-scenes.  The paper prints no numeric example of them; every other function is pinned by
-closed forms, invariants or brute force in ``tests/test_oracle_*.py``.
+scenes; the paper prints no numeric example of them.  The per-step functions are pinned
+by closed forms, invariants or brute force in ``tests/test_oracle_*.py``: among them the
+DFSPH factor alpha (``test_oracle_alpha.py``: the lattice closed form, and one Jacobi
+update cancelling a lone compression next to a wall exactly), the hydrostatic pressure
+gradient within 5 % and the depth-independent buoyancy of a submerged body.
 """
 from __future__ import annotations
 

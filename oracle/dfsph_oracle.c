@@ -21,10 +21,13 @@
  * and pressure-acceleration building blocks.
  *
  * Pins (see tests/test_oracle_*.py): kernel normalisation and gradient antisymmetry,
- * lattice rest density, brute-force neighbour sets, momentum antisymmetry of pressure,
- * viscosity and boundary forces, hydrostatic pressure in a resting tank, operator
- * symmetry of implicit viscosity, MLP gradients against finite differences, and a run
- * resumed through the state setters (fluid and rigid) continuing bit for bit.
+ * lattice rest density, the DFSPH factor alpha (closed-form lattice value, and the exact
+ * cancellation of a lone compression next to a wall by one Jacobi update), brute-force
+ * neighbour sets, momentum antisymmetry of pressure, viscosity and boundary forces,
+ * hydrostatic pressure in a resting tank (weight on the walls, interior gradient within
+ * 5 %), depth-independent buoyancy of a submerged body, operator symmetry of implicit
+ * viscosity, MLP gradients against finite differences, and a run resumed through the
+ * state setters (fluid and rigid) continuing bit for bit.
  */
 #include <math.h>
 #include <stdint.h>

@@ -3,8 +3,8 @@
 Rest density on a full lattice (closed form), momentum antisymmetry of the pressure
 acceleration (Sec. 3.3 Eq. pressure_acceleration), zero modes and dissipation of the
 explicit viscosity (Sec. 3.6.1 Eq. lap), convergence of the Jacobi PPE loop (Alg.
-ppe_solver), hydrostatic equilibrium in a resting tank (force balance and pressure
-gradient), bookkeeping of the Akinci boundary impulse (Sec. 3.5), mass conservation.
+ppe_solver), hydrostatic equilibrium in a resting tank (force balance and a 5 % interior
+pressure gradient), bookkeeping of the Akinci boundary impulse (Sec. 3.5), mass conservation.
 """
 import math
 
@@ -153,29 +153,45 @@ def test_divergence_free_at_rest(oracle_lib):
 
 
 def test_hydrostatic_equilibrium(oracle_lib):
-    d = scenes.resting_tank(n=(8, 8, 12), dt_max=1e-3, viscosity=0.05)
+    d = scenes.resting_tank(n=(12, 12, 16), dt_max=1e-3, viscosity=0.05)
     s = oracle_lib.Scene(d)
     for _ in range(300):
         s.step(0.0)
     F = np.zeros(3)
     P = np.zeros(len(d["fluid_x"]))
-    Z = np.zeros_like(P)
+    X = np.zeros((len(P), 3))
     K = 200
     for _ in range(K):
         s.step(0.0)
         F += s.get(oracle_lib.FB_IMPULSE).sum(0) / s.stats()["dt"]
-        P += s.get(oracle_lib.PRESSURE)
-        Z += s.get(oracle_lib.X)[:, 2]
-    F, P, Z = F / K, P / K, Z / K
+        # the step's pressure impulse is split between the density solve and the
+        # divergence solve, and both apply kappa through the same update (Eq.
+        # pressure_acceleration with p/rho^2 = kappa/rho): the hydrostatic pressure is
+        # (kappa_sum + kappa_v_sum) rho
+        P += (s.get(oracle_lib.KAPPA) + s.get(oracle_lib.KAPPA_V)) * s.get(oracle_lib.RHO)
+        X += s.get(oracle_lib.X)
+    F, P, X = F / K, P / K, X / K
     weight = s.mass * len(P) * 9.81
     # the walls carry the weight (momentum balance of a fluid at rest)
     assert F[2] / weight == pytest.approx(1.0, abs=0.01)
     assert abs(F[0]) < 0.01 * weight and abs(F[1]) < 0.01 * weight
-    # interior pressure gradient is rho0 g (layers 2 spacings above the floor and
-    # below the surface; Jacobi DFSPH pressure alternates by layer, so fit a line)
-    sel = (Z > Z.min() + 0.035) & (Z < Z.max() - 0.035)
-    slope = np.polyfit(Z[sel], P[sel], 1)[0]
-    assert -slope / (1000.0 * 9.81) == pytest.approx(1.0, abs=0.2)
+    # interior pressure gradient is rho0 g: columns more than 1.75 spacings from the
+    # outermost ones, layers from the second above the floor to the third below the
+    # surface.  Jacobi DFSPH pressure alternates between adjacent layers (the SPH
+    # gradient barely sees a mode of the particle spacing), so the layer means are
+    # averaged in adjacent pairs before the line fit.
+    Z = X[:, 2]
+    layer = np.round((Z - Z.min()) / 0.02).astype(int)
+    lo, hi = X[:, :2].min(0) + 0.035, X[:, :2].max(0) - 0.035
+    inner = np.all((X[:, :2] > lo) & (X[:, :2] < hi), axis=1)
+    top = layer.max()
+    ks = list(range(1, top - 1))
+    ks = ks[: len(ks) // 2 * 2]
+    pm = [P[inner & ((layer == k) | (layer == k + 1))].mean() for k in ks[::2]]
+    zm = [Z[inner & ((layer == k) | (layer == k + 1))].mean() for k in ks[::2]]
+    slope = np.polyfit(zm, pm, 1)[0]
+    assert len(pm) >= 6
+    assert -slope / (1000.0 * 9.81) == pytest.approx(1.0, abs=0.05)
 
 
 def test_boundary_impulse_bookkeeping(oracle_lib):
