@@ -413,12 +413,27 @@ sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
  * SPH_NOALLOC_MAX_POINTS or a grid above SPH_NOALLOC_MAX_CELLS cells returns SPH_EINVAL,
  * and calls whose work overlaps on the GPU (different streams, or host threads) race on
  * that array.  The first call on a device looks up the array's device address (with that
- * device current) and should come before any stream capture.  Calls no allocator. */
+ * device current) and should come before any stream capture.  Calls no allocator.
+ * Points outside [domain_min, domain_max] (and NaN coordinates) are clamped into the edge
+ * cells of the padded grid, as in sph_step.  The order inside a cell is found by counting,
+ * per point, the cell's smaller indices, so the work grows with the square of a cell's
+ * occupancy: many points clamped into a few cells make the call slow.
+ * SPH_OK means the work was enqueued; whether its prefix scan completed is reported by
+ * sph_grid_order_noalloc_status. */
 #define SPH_NOALLOC_MAX_POINTS 262144
 #define SPH_NOALLOC_MAX_CELLS 1048576
 sph_status sph_grid_order_noalloc(const float *x, int64_t n, const float *domain_min,
                                   const float *domain_max, float cell_size, int32_t *order,
                                   uint32_t *keys, void *stream);
+
+/* Outcome of the last sph_grid_order_noalloc call on the current device: synchronises
+ * stream (the one that call used), then reads the scratch array's error word into host
+ * memory with a copy from the symbol (no allocation).  SPH_ETIMEOUT: a bounded wait of the
+ * call's look-back prefix scan ran out, so its order is not valid (the GPU stays usable);
+ * SPH_OK: it completed; SPH_ECUDA: the synchronisation or the copy failed.  The word is
+ * cleared by every call, so a later or overlapping call replaces it.  Not for use inside a
+ * stream capture (it synchronises). */
+sph_status sph_grid_order_noalloc_status(void *stream);
 
 /* Post-processing (Sec. 4.3: surface reconstruction of the fluid particles, then rendering;
  * the paper uses SplashSurf and Blender, these are CUDA kernels writing device buffers).

@@ -1327,32 +1327,40 @@ sph_status sph_write_state(sph_ctx *c, int32_t scene, const float *x, const floa
     const int64_t nf = q.nf;
     cudaStream_t s = c->stream;
     int blocks = (int)((nf + 255) / 256);
+    // host inputs are staged into one device buffer before anything of the scene changes,
+    // so that a failed staging leaves it as it was; the buffer is freed on every exit
+    struct Stage {
+        float *p = nullptr;
+        cudaStream_t s;
+        ~Stage() { if (p) cudaFreeAsync(p, s); }
+    } stage{nullptr, s};
+    const float *dx = x, *dv = v;
+    if (!on_device && (x || v)) {
+        if (cudaMallocAsync(&stage.p, 24 * (size_t)nf, s) != cudaSuccess) {
+            stage.p = nullptr;
+            return fail(c, SPH_ECUDA, "write_state staging failed");
+        }
+        if (x) {
+            if (cudaMemcpyAsync(stage.p, x, 12 * nf, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return fail(c, SPH_ECUDA, "write_state staging failed");
+            dx = stage.p;
+        }
+        if (v) {
+            if (cudaMemcpyAsync(stage.p + 3 * nf, v, 12 * nf, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return fail(c, SPH_ECUDA, "write_state staging failed");
+            dv = stage.p + 3 * nf;
+        }
+    }
     k_unpermute_to_sorted<<<blocks, 256, 0, s>>>(c->P, scene);
     k_sorted_to_canonical<<<blocks, 256, 0, s>>>(c->P, scene);
     if ((st = check_async(c)) != SPH_OK) return st;
-    float *stage = nullptr;
-    auto stage_in = [&](const float *src, size_t bytes) -> const float * {
-        if (on_device) return src;
-        if (!stage && cudaMallocAsync(&stage, 12 * (size_t)nf, s) != cudaSuccess) return nullptr;
-        if (cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
-        return stage;
-    };
-    if (x) {
-        const float *d = stage_in(x, 12 * nf);
-        if (!d) return fail(c, SPH_ECUDA, "write_state staging failed");
-        k_pack3<<<blocks, 256, 0, s>>>(c->P.pos_c + q.f_off, d, nf, 0.0f);
-    }
-    if (v) {
-        const float *d = stage_in(v, 12 * nf);
-        if (!d) return fail(c, SPH_ECUDA, "write_state staging failed");
-        k_pack3<<<blocks, 256, 0, s>>>(c->P.vel_c + q.f_off, d, nf, 0.0f);
-    }
+    if (x) k_pack3<<<blocks, 256, 0, s>>>(c->P.pos_c + q.f_off, dx, nf, 0.0f);
+    if (v) k_pack3<<<blocks, 256, 0, s>>>(c->P.vel_c + q.f_off, dv, nf, 0.0f);
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (kappa_prev) CK(cudaMemcpyAsync(c->P.kprev_c + q.f_off, kappa_prev, 4 * nf, kind, s));
     if (kappa_v_prev) CK(cudaMemcpyAsync(c->P.kvprev_c + q.f_off, kappa_v_prev, 4 * nf, kind, s));
     k_scene_cfl<<<1, 256, 0, s>>>(c->P, scene);
     if ((st = check_async(c)) != SPH_OK) return st;
-    if (stage) CK(cudaFreeAsync(stage, s));
     CK(cudaStreamSynchronize(s));
     return SPH_OK;
 }

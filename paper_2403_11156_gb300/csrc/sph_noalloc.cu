@@ -13,6 +13,7 @@
 #include "sph_internal.cuh"
 
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 
 using namespace sph;
@@ -162,4 +163,17 @@ extern "C" sph_status sph_grid_order_noalloc(const float *x, int64_t n, const fl
     k_na_scatter<<<bp, t, 0, s>>>(v, n);
     k_na_rank<<<bp, t, 0, s>>>(v, n, order);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;
+}
+
+extern "C" sph_status sph_grid_order_noalloc_status(void *stream)
+{
+    // the scan's bounded waits record a timeout in the scratch's control word, which each
+    // call clears before its scan: read it back once the stream's work is done (a copy
+    // from the symbol into a host integer, nothing allocated)
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SPH_ECUDA;
+    int32_t err = 0;
+    const size_t off = kOffCtl + offsetof(Control, error);
+    if (cudaMemcpyFromSymbol(&err, g_grid_scratch, sizeof(err), off, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SPH_ECUDA;
+    return err != 0 ? SPH_ETIMEOUT : SPH_OK;
 }

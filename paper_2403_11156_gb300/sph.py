@@ -159,6 +159,7 @@ def load():
     L.sph_last_error.argtypes = [vp]
     L.sph_destroy.argtypes = [vp]
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
+    L.sph_grid_order_noalloc_status.argtypes = [vp]
     L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
     L.sph_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.sph_set_trace.argtypes = [vp, ip]
@@ -173,7 +174,7 @@ def load():
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats", "sph_probe_wait_timeout",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
+                 "sph_grid_order_noalloc", "sph_grid_order_noalloc_status", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
                  "sph_read_trace", "sph_surface_field", "sph_surface_mesh", "sph_render_heightmap"):
         getattr(L, name).restype = C.c_int32
     _lib = L
@@ -472,6 +473,13 @@ def sph_grid_order_noalloc(x, n, domain_min, domain_max, cell_size, order, keys=
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     return load().sph_grid_order_noalloc(ptr(x), int(n), lo, hi, float(cell_size), ptr(order),
                                          ptr(keys), st)
+
+
+def sph_grid_order_noalloc_status(stream=None):
+    """Marshal sph_grid_order_noalloc_status: SPH_OK once the last call's work on `stream`
+    completed with its prefix scan, SPH_ETIMEOUT if a wait of that scan ran out."""
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return load().sph_grid_order_noalloc_status(st)
 
 
 def sph_surface_mesh(field, origin, spacing, iso=0.5, cap=None, stream=None):

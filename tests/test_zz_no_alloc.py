@@ -1,13 +1,16 @@
 """sph_grid_order_noalloc: the neighbour-search grid order for callers that cannot let a
 library allocate device memory (work enqueued during another component's CUDA-graph
 capture, applications that own the GPU memory budget, real-time loops).  Checked through
-the C ABI against the grid order and cell keys that the regular path (sph_create +
-sph_step) reports for the same positions, on two calls in a row that share the static
-scratch array.  Collected last so that a stop-at-first-failure run has already run the
-rest of the suite."""
+the C ABI against the oracle's cell keys and (cell key, index) order (the float cell-key
+contract of the neighbour search, bit-exact), on two calls in a row that share the static
+scratch array, with points outside the domain clamped into the edge cells; and against
+the grid order the regular path (sph_create + sph_step) reports for the same positions.
+Collected last so that a stop-at-first-failure run has already run the rest of the
+suite."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2403_11156_gb300 import scenes, sph
 
 from gpu_util import gpu_ctx
@@ -15,33 +18,49 @@ from gpu_util import gpu_ctx
 pytestmark = pytest.mark.gpu
 
 
-def _reference(d):
-    g = gpu_ctx(d)
-    g.sph_step(4e-4)
-    g.sph_synchronize(raise_on_error=False)
-    order = g.sph_read_field(sph.FIELD_SORTED_ID)
-    keys = g.sph_read_field(sph.FIELD_CELL_KEY)
-    g.close()
-    return order, keys
+def _run(x_np, dmin, dmax, cell, stream):
+    import torch
+    n = len(x_np)
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    keys = torch.zeros(n, dtype=torch.int32, device="cuda")
+    st = sph.sph_grid_order_noalloc(x, n, dmin, dmax, np.float32(cell), order, keys, stream)
+    assert st == sph.SPH_OK
+    assert sph.sph_grid_order_noalloc_status(stream) == sph.SPH_OK
+    return order.cpu().numpy(), keys.cpu().numpy().view(np.uint32)
+
+
+def test_noalloc_grid_order_matches_oracle():
+    import torch
+    d = scenes.dam_break_small()                      # 8,000 points
+    x = np.array(d["fluid_x"])
+    # a few points outside the domain (and on its faces): clamped into the edge cells
+    x[:6] = np.array([[-0.3, 0.2, 0.2], [0.9, 0.2, 0.2], [0.2, -1.0, 0.2],
+                      [0.2, 0.2, 5.0], [0.0, 0.0, 0.0], [0.8, 0.8, 0.8]], np.float32)
+    cell = oracle.default_cell_size(d["radius"])
+    keys_o = oracle.cell_keys(x, d["domain_min"], d["domain_max"], cell)
+    order_o = oracle.sort_order(keys_o)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):                                # the second call reuses the scratch
+        order, keys = _run(x, d["domain_min"], d["domain_max"], cell, stream)
+        np.testing.assert_array_equal(keys, keys_o)
+        np.testing.assert_array_equal(order, order_o)
 
 
 def test_noalloc_grid_order_matches_regular_path():
     import torch
-    d = scenes.dam_break_small()                      # 8,000 points
-    order_ref, keys_ref = _reference(d)
-    cell = np.float32(np.float32(4.0) * np.float32(d["radius"])) * np.float32(1.00390625)
-    x = torch.from_numpy(np.ascontiguousarray(d["fluid_x"])).cuda()
-    n = len(d["fluid_x"])
-    stream = torch.cuda.current_stream()
-    for _ in range(2):                                # the second call reuses the scratch
-        order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-        keys = torch.zeros(n, dtype=torch.int32, device="cuda")
-        st = sph.sph_grid_order_noalloc(x, n, d["domain_min"], d["domain_max"], np.float32(cell),
-                                        order, keys, stream)
-        assert st == sph.SPH_OK
-        torch.cuda.synchronize()
-        np.testing.assert_array_equal(order.cpu().numpy(), order_ref)
-        np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint32), keys_ref)
+    d = scenes.dam_break_small(seed=4, n=(12, 14, 10))
+    g = gpu_ctx(d)
+    g.sph_step(4e-4)
+    g.sph_synchronize(raise_on_error=False)
+    order_ref = g.sph_read_field(sph.FIELD_SORTED_ID)
+    keys_ref = g.sph_read_field(sph.FIELD_CELL_KEY)
+    g.close()
+    cell = oracle.default_cell_size(d["radius"])
+    order, keys = _run(d["fluid_x"], d["domain_min"], d["domain_max"], cell,
+                       torch.cuda.current_stream())
+    np.testing.assert_array_equal(order, order_ref)
+    np.testing.assert_array_equal(keys, keys_ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
