@@ -182,22 +182,42 @@ __global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P
                 const int64_t row = sc.c_off + (int64_t)sc.dims[0] * (y + (int64_t)sc.dims[1] * z);
                 const uint32_t jb = P.cell_start[row + x0], je = P.cell_start[row + x1 + 1];
                 if constexpr (T == 1) {
-                    // only the stencil's centre row holds the particle itself: the other
-                    // rows skip the self test
-                    // the append is branch-free: a predicated store through a running
-                    // slot pointer, so most candidates (rejected) cost no divergence
-                    auto scan = [&](auto check_self) {
-                        for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
-                            float dx, dy2, dz2;
-                            const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
-                            const bool hit = d2 < h2 && (!decltype(check_self)::value || j != self);
-                            if (hit && nn_f < cap_f) *slot_f = (int32_t)j;
-                            slot_f += hit ? NF : 0;
-                            nn_f += hit;
-                        });
-                    };
-                    if (dz == 0 && dy == 0) scan(std::true_type{});
-                    else scan(std::false_type{});
+                    if (je - jb <= 64u) {
+                        // a row of up to 64 candidates: the predicate only sets bits of a
+                        // mask (no store or counter per candidate, most are rejected), and
+                        // the hits are appended in candidate order from the mask
+                        auto bits = [&](uint32_t b0, uint32_t b1) {
+                            uint32_t mk = 0u;
+                            for_range<4, 1>(P.pos_s, b0, b1, [&](uint32_t j, float4 pj) {
+                                float dx, dy2, dz2;
+                                mk |= (uint32_t)(pred_d2(pi, pj, dx, dy2, dz2) < h2) << (j - b0);
+                            });
+                            return mk;
+                        };
+                        uint64_t m = bits(jb, min(je, jb + 32u));
+                        if (je > jb + 32u) m |= (uint64_t)bits(jb + 32u, je) << 32;
+                        // only the stencil's centre row holds the particle itself
+                        if (dz == 0 && dy == 0) m &= ~(1ull << (self - jb));
+                        for (; m != 0ull; m &= m - 1ull) {
+                            if (nn_f < cap_f) *slot_f = (int32_t)(jb + (uint32_t)(__ffsll((long long)m) - 1));
+                            slot_f += NF;
+                            ++nn_f;
+                        }
+                    } else {
+                        // longer rows: a predicated store through a running slot pointer
+                        auto scan = [&](auto check_self) {
+                            for_range<4, 1>(P.pos_s, jb, je, [&](uint32_t j, float4 pj) {
+                                float dx, dy2, dz2;
+                                const float d2 = pred_d2(pi, pj, dx, dy2, dz2);
+                                const bool hit = d2 < h2 && (!decltype(check_self)::value || j != self);
+                                if (hit && nn_f < cap_f) *slot_f = (int32_t)j;
+                                slot_f += hit ? NF : 0;
+                                nn_f += hit;
+                            });
+                        };
+                        if (dz == 0 && dy == 0) scan(std::true_type{});
+                        else scan(std::false_type{});
+                    }
                 } else {
                     // the group's lanes test T consecutive candidates at a time and append the
                     // hits in candidate order; full batches of kCand groups load all their

@@ -89,15 +89,32 @@ __device__ __forceinline__ unsigned group_mask()
 // lane's last entry.  NC: the list is read-only for the kernel (read-only data path);
 // otherwise plain loads, for a list this warp has just written.  Visiting order = list
 // order.
+// A read-only list is streamed once per sweep: its loads bypass L1 and are marked first for
+// eviction in L2, so that they do not displace the particles' positions and velocities
+// (the gathered data, which the sweeps reuse from L2).
+__device__ __forceinline__ uint64_t stream_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 template <int U, int T, bool NC = true, typename F>
 __device__ __forceinline__ void for_list(const int32_t *__restrict__ list, int64_t NF, int64_t i, int s, int n,
                                          F &&visit)
 {
     const int m = n > s ? (n - s + T - 1) / T : 0;   // this lane's entries
     if (m <= 0) return;
+    const uint64_t pol = NC ? stream_policy() : 0ull;
     auto ld = [&](int k) {
         const int64_t a = (int64_t)(s + T * min(k, m - 1)) * NF + i;
-        return NC ? __ldg(list + a) : list[a];
+        return NC ? ld_stream(list + a, pol) : list[a];
     };
     int32_t j[U];
 #pragma unroll
