@@ -51,12 +51,25 @@ ALGO_BYTES = {
 BOUNDARY_BYTES = 16                             # x_b, Psi_b per boundary particle and sweep
 # DRAM bytes (read + write) per launch measured by ncu on this workload at 1 thread per
 # particle, gather batch 4 and cell size h (1 + 2^-8), for the kernels as they are built
-# now (the roofline's `traffic`; null for any other kernel or configuration).
-TRAFFIC = {("dens_pass_a", 1, 4, 27): 211.56e6 + 16.68e6}
+# now (the roofline's `traffic`; null for any other kernel or configuration).  Filled from
+# the committed captures (profiles/*_dam_break_1.2M.md); a kernel changed since its capture
+# has no entry.
+TRAFFIC = {("density_alpha", 1, 4, 27): 81.43e6 + 168.60e6,
+           ("dens_pass_a", 1, 4, 27): 211.59e6 + 4.72e6,
+           ("dens_pass_b", 1, 4, 27): 199.66e6 + 3.99e6}
 # FP32 operations per neighbour pair in the list sweeps (distance, spline gradient, dot)
 FLOPS_PER_PAIR = {"dens_pass_a": 26, "div_pass_a": 24, "dens_pass_b": 22, "div_pass_b": 22,
                   "dens_warm_pass_b": 22, "div_warm_pass_b": 22, "nonpressure": 30,
-                  "warm_density": 26}
+                  "warm_density": 26, "density_alpha": 40}
+# extra FP32 operations per fluid particle outside the pair sums: the density sweep's
+# candidate tests (about 216 per particle at 8 flop each: 3 differences, 3 products, 2 sums)
+FLOPS_PER_PARTICLE = {"density_alpha": 216 * 8}
+# the kernels reported with a roofline of their own (the step's three largest)
+ROOFLINE_KERNELS = ("density_alpha", "dens_pass_a", "dens_pass_b")
+# launches per step of a kernel in the timed region, from the solver iteration counts
+# (the eager timing pass runs later steps, whose iteration counts differ)
+PER_DENSITY_ITERATION = ("dens_pass_a", "dens_pass_b", "dens_check")
+PER_DIVERGENCE_ITERATION = ("div_pass_a", "div_pass_b", "div_check")
 
 
 def load_peaks():
@@ -170,7 +183,9 @@ def learned_vs_plain():
     out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(big, params, steps=200)
     for mode in out["dam_break_1.2M_rigid"].values():
         mode["particle_steps_per_s"] = len(big["fluid_x"]) / (mode["ms_per_step"] / 1000.0)
-    for res in (out["eta_1e-3"], out["dam_break_1.2M_rigid"]):
+    for res in (out["eta_1e-3"], out["eta_1e-5"], out["dam_break_1.2M_rigid"]):
+        # the solves' iteration floor: at least 2 density and 1 divergence iterations per step
+        res["iteration_floor"] = {"density": 2, "divergence": 1}
         p, l = res["previous"], res["learned"]
         res["learned_over_previous"] = {
             "density_iteration_ratio": p["density_iters_per_step"] / l["density_iters_per_step"],
@@ -178,6 +193,35 @@ def learned_vs_plain():
                                       (l["density_iters_per_step"] + l["divergence_iters_per_step"]),
             "time_ratio": p["ms_per_step"] / l["ms_per_step"]}
     return out, params
+
+
+def learned_headline(desc, params, steps, warmup, autotune, stream):
+    """The benchmark workload with the learned warm start, over the same region as the
+    plain `value`: `warmup` untimed graph steps from the same initial state, then `steps`
+    graph steps timed with CUDA events on the library stream."""
+    import torch
+    from paper_2403_11156_gb300 import scenes, sph
+    d = dict(desc)
+    d["warm_start"] = scenes.WARM_LEARNED
+    n = len(d["fluid_x"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with sph.Context(d, stream=stream, autotune=autotune) as g:
+        g.sph_set_mlp(params)
+        g.sph_steps(warmup, 0.0)
+        g.sph_synchronize(raise_on_error=False)
+        s0 = g.sph_get_stats()
+        torch.cuda.synchronize()
+        a.record(stream)
+        g.sph_steps(steps, 0.0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        status = g.sph_synchronize(raise_on_error=False)
+        s1 = g.sph_get_stats()
+    ms = a.elapsed_time(b) / steps
+    return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "mean_density_iters": (s1["total_dens_iters"] - s0["total_dens_iters"]) / steps,
+            "mean_divergence_iters": (s1["total_div_iters"] - s0["total_div_iters"]) / steps,
+            "final_density_error": s1["dens_err"], "status": sph.STATUS_NAMES[status]}
 
 
 def batched_learned(params, steps=200):
@@ -511,17 +555,15 @@ def main():
     ms, units = reduce_timing(ms, n_fluid * args.steps, world, device="cuda")
     value = units / (ms / 1000.0)
 
-    # ---- end to end through the C ABI: each step enqueued with a host dt and its
-    # positions read back into pinned host memory
-    # the same K steps from the same initial state on a second context (same, cached
-    # tuning), each step's positions read back: double-buffered, the positions of step k
-    # are snapshotted on the library stream and copied to pinned host memory on a copy
-    # stream while step k + 1 runs; the host waits for step k - 2's copy before reusing its
-    # buffers, and for the last ones at the end
+    # ---- end to end through the C ABI: the same K steps from the same initial state on a
+    # second context (same, cached tuning).  Every step is enqueued with its host dt and
+    # its result, all positions in original particle order, is read into page-locked host
+    # memory by sph_read_state (on_device = 3: the unpermute and the device-to-host copy
+    # follow the step on the library stream).  The host stays one step ahead: before
+    # reusing a host buffer it waits for the event recorded after the read of two steps
+    # earlier.  The scene is resident on the device (uploaded once at create, outside the
+    # timed region); per step the host supplies dt (4 B) and receives 12 B per particle.
     pinned = [torch.empty((n_fluid, 3), dtype=torch.float32, pin_memory=True) for _ in range(2)]
-    dev_x = [torch.empty((n_fluid, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    ready = [torch.cuda.Event() for _ in range(2)]
     done = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = args.steps
     g2 = sph.Context(desc, stream=stream, autotune=not args.no_autotune)
@@ -535,65 +577,101 @@ def main():
         if k >= 2:
             done[b].synchronize()                   # step k - 2's positions are on the host
         g2.sph_step(0.0)
-        g2.sph_read_state_device(0, x=dev_x[b], sync=False)
-        ready[b].record(stream)
-        copy_stream.wait_event(ready[b])
-        with torch.cuda.stream(copy_stream):
-            pinned[b].copy_(dev_x[b], non_blocking=True)
-        done[b].record(copy_stream)
+        g2.sph_read_state_host(0, x=pinned[b], sync=False)
+        done[b].record(stream)
     for b in range(2):
         done[b].synchronize()
+    e2e_wall = time.perf_counter() - t
+    x_e2e = pinned[(e2e_steps - 1) % 2].numpy().copy()
     g2.close()
-    e2e_ms, e2e_units = reduce_timing((time.perf_counter() - t) * 1000.0, n_fluid * e2e_steps, world,
-                                      device="cuda")
+    e2e_ms, e2e_units = reduce_timing(e2e_wall * 1000.0, n_fluid * e2e_steps, world, device="cuda")
     e2e = {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 4,
-           "d2h_bytes_per_step": 12 * n_fluid}
+           "d2h_bytes_per_step": 12 * n_fluid,
+           "path": "sph_step + sph_read_state(on_device = 3) into page-locked host memory",
+           "last_positions_finite": bool(np.all(np.isfinite(x_e2e)))}
 
-    # ---- kernel breakdown: eager steps with CUDA events around every launch
+    # ---- kernel breakdown: eager steps with CUDA events around every launch (graph kernel
+    # nodes cannot be bracketed by events).  Per-launch times come from these steps; the
+    # time per step of each kernel weights them by its launches per step in the timed
+    # region (solver passes by that region's mean iteration counts), which picks the
+    # dominant kernel of the timed region's regime.
     g.sph_set_mode(graph=False, timing=True)
     g.sph_kernel_times(reset=True)
+    it_t0 = g.sph_get_stats()
     g.sph_steps(args.timing_steps, 0.0)
     g.sph_synchronize(raise_on_error=False)
+    it_t1 = g.sph_get_stats()
     kt = g.sph_kernel_times(reset=True)
     g.sph_set_mode(graph=True, timing=False)
-    total_ms = sum(v[1] for v in kt.values())
-    top = max(kt.items(), key=lambda t: t[1][1])
-    name, (n_launch, k_ms) = top
-    per_launch_s = k_ms / n_launch / 1000.0
+    dens_per_step = (it1["total_dens_iters"] - it0["total_dens_iters"]) / args.steps
+    div_per_step = (it1["total_div_iters"] - it0["total_div_iters"]) / args.steps
+    per_step_launch = {}
+    for k_name, (n_launch, _) in kt.items():
+        if k_name in PER_DENSITY_ITERATION:
+            per_step_launch[k_name] = dens_per_step
+        elif k_name in PER_DIVERGENCE_ITERATION:
+            per_step_launch[k_name] = div_per_step
+        else:
+            per_step_launch[k_name] = n_launch / args.timing_steps
+    per_step_ms = {k_name: v[1] / v[0] * per_step_launch[k_name] for k_name, v in kt.items() if v[0]}
+    total_ms = sum(per_step_ms.values())
     n_b = len(desc["boundary_x"])
     hbm, sm_max, peak_src = load_peaks()
-    algo = ALGO_BYTES.get(name, 48) * n_fluid + BOUNDARY_BYTES * n_b
-    achieved_gbs = algo / per_launch_s / 1e9
-    nbr = float(it1["max_fluid_nbrs"])
-    roof = {"kernel": name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": achieved_gbs / hbm,
-            "traffic": TRAFFIC.get((name, tuning.get("lanes"), tuning.get("gather_batch"),
-                                    27 if float(tuning.get("cell_factor", 0.0)) > 0.75 else 125)),
-            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured" else "fallback 6.8 TB/s",
-            "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
-            "share_of_step": k_ms / total_ms if total_ms else None}
-    if roof["traffic"]:
-        # the DRAM rate the launch actually sustains: ncu's bytes per launch (the algorithmic
-        # state plus the neighbour-list stream) over the live launch time
-        roof["traffic_gbs"] = roof["traffic"] / per_launch_s / 1e9
-        roof["traffic_frac"] = roof["traffic_gbs"] / hbm
-    if name in FLOPS_PER_PAIR:
-        # ALU view of the same kernel: counted FP32 flops over the measured mean neighbour count
-        nn_mean = 33.0
-        flops = FLOPS_PER_PAIR[name] * nn_mean * n_fluid
-        roof["alu"] = {"achieved_tflops": flops / per_launch_s / 1e12,
-                       "peak_tflops": fp32_peak_tflops(clocks.summary().get("sm_mhz") or sm_max),
-                       "pairs_per_particle": nn_mean}
-        roof["alu"]["frac"] = roof["alu"]["achieved_tflops"] / roof["alu"]["peak_tflops"]
-    breakdown = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_ms, 4)}
-                 for k, v in sorted(kt.items(), key=lambda t: -t[1][1])}
+    sm_mhz = clocks.summary().get("sm_mhz") or sm_max
+    cfg_key = (tuning.get("lanes"), tuning.get("gather_batch"),
+               27 if float(tuning.get("cell_factor", 0.0)) > 0.75 else 125)
+    nn_mean = float(g.sph_read_field(sph.FIELD_NN_FLUID).mean())
 
+    def roofline(name):
+        n_launch, k_ms = kt[name]
+        per_launch_s = k_ms / n_launch / 1000.0
+        algo = ALGO_BYTES.get(name, 48) * n_fluid + BOUNDARY_BYTES * n_b
+        achieved_gbs = algo / per_launch_s / 1e9
+        r = {"kernel": name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+             "frac": achieved_gbs / hbm, "traffic": TRAFFIC.get((name,) + cfg_key),
+             "peak_source": ("%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
+                             else "fallback 6.8 TB/s"),
+             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
+             "launches_per_step": per_step_launch[name],
+             "share_of_step": per_step_ms[name] / total_ms if total_ms else None}
+        if r["traffic"]:
+            # the DRAM rate the launch sustains: ncu's bytes per launch over the live time
+            r["traffic_gbs"] = r["traffic"] / per_launch_s / 1e9
+            r["traffic_frac"] = r["traffic_gbs"] / hbm
+        if name in FLOPS_PER_PAIR:
+            # ALU view: counted FP32 flops (pairs at the step's mean neighbour count, plus
+            # the density sweep's candidate tests) over the FP32 peak at the sampled clock
+            flops = (FLOPS_PER_PAIR[name] * nn_mean + FLOPS_PER_PARTICLE.get(name, 0)) * n_fluid
+            r["alu"] = {"achieved_tflops": flops / per_launch_s / 1e12,
+                        "peak_tflops": fp32_peak_tflops(sm_mhz), "pairs_per_particle": nn_mean}
+            r["alu"]["frac"] = r["alu"]["achieved_tflops"] / r["alu"]["peak_tflops"]
+        return r
+
+    top_name = max(per_step_ms.items(), key=lambda t: t[1])[0]
+    roof = roofline(top_name)
+    rooflines = {k_name: roofline(k_name) for k_name in ROOFLINE_KERNELS if k_name in kt}
+    breakdown = {k_name: {"launches_timing_pass": kt[k_name][0], "launches_per_step": round(per_step_launch[k_name], 3),
+                          "us_per_launch": round(1000.0 * kt[k_name][1] / kt[k_name][0], 2),
+                          "ms_per_step": round(v, 4), "share": round(v / total_ms, 4)}
+                 for k_name, v in sorted(per_step_ms.items(), key=lambda t: -t[1])}
+
+    d_it = it1["total_dens_iters"] - it0["total_dens_iters"]
+    v_it = it1["total_div_iters"] - it0["total_div_iters"]
     post = None
     if rank == 0 and not args.no_batched:
         post = post_processing(g, desc, stream)
     learned = None
+    learned_line = None
     if rank == 0 and not args.no_learned:
         learned, params = learned_vs_plain()
+        # the metric's other half: the same workload and timed region with the learned start
+        learned_line = learned_headline(desc, params, args.steps, args.warmup, not args.no_autotune, stream)
+        plain_iters = (d_it + v_it) / args.steps
+        learned_iters = learned_line["mean_density_iters"] + learned_line["mean_divergence_iters"]
+        learned_line["over_plain"] = {
+            "value_ratio": learned_line["value"] / value,
+            "density_iteration_ratio": (d_it / args.steps) / max(learned_line["mean_density_iters"], 1e-9),
+            "solver_iteration_ratio": plain_iters / max(learned_iters, 1e-9)}
         if not args.no_batched:
             learned["batched_64_scenes"] = batched_learned(params)
     batched = None
@@ -614,8 +692,6 @@ def main():
         g.close()
         cpu = cpu_baseline(desc)
 
-    d_it = it1["total_dens_iters"] - it0["total_dens_iters"]
-    v_it = it1["total_div_iters"] - it0["total_div_iters"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -628,7 +704,8 @@ def main():
                    "final_density_error": it1["dens_err"], "dt": it1["dt"], "status": sph.STATUS_NAMES[status],
                    "autotune": tuning},
         "clocks": clocks.summary(), "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
-        "kernels": breakdown, "cpu_baseline": cpu, "learned_vs_plain": learned,
+        "rooflines": rooflines, "kernels": breakdown, "cpu_baseline": cpu, "learned": learned_line,
+        "learned_vs_plain": learned,
         "batched_64_scenes": batched,
         "wcsph_1.2M": wcsph,
         "viscous_column_250k": column,

@@ -211,7 +211,11 @@ sph_status sph_synchronize(sph_ctx *ctx);
  * step).  on_device == 0: host memory, synchronises; 1: device memory, synchronises;
  * 2: device memory, only enqueued on the context's stream (order later work after it with
  * an event on that stream), so a caller can copy a step's result out while the next step
- * runs. */
+ * runs; 3: host memory, only enqueued (the device-to-host copies follow the step on the
+ * context's stream: with page-locked host buffers the call returns at once and the data
+ * is there once the stream has passed this point, which an event recorded on the stream
+ * after the call or sph_synchronize tells; with pageable buffers the copies wait for the
+ * stream).  Other values: SPH_EINVAL. */
 sph_status sph_read_state(sph_ctx *ctx, int32_t scene, float *x, float *v, float *rho,
                           float *pressure, int32_t on_device);
 

@@ -1260,7 +1260,8 @@ static sph_status read_into(sph_ctx *c, int32_t scene, int field, void *out, siz
     if (n == 0) return SPH_OK;
     void *dst = out;
     void *tmp = nullptr;
-    if (!on_device) {
+    const bool host = on_device == 0 || on_device == 3;
+    if (host) {
         CK(cudaMallocAsync(&tmp, bytes, c->stream));
         dst = tmp;
     }
@@ -1269,7 +1270,7 @@ static sph_status read_into(sph_ctx *c, int32_t scene, int field, void *out, siz
     else k_read_fluid<<<blocks, 256, 0, c->stream>>>(c->P, scene, field, dst);
     sph_status st = check_async(c);
     if (st != SPH_OK) return st;
-    if (!on_device) {
+    if (host) {
         CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaFreeAsync(tmp, c->stream));
     }
@@ -1281,12 +1282,13 @@ sph_status sph_read_state(sph_ctx *c, int32_t scene, float *x, float *v, float *
 {
     sph_status st = scene_ok(c, scene);
     if (st != SPH_OK) return st;
+    if (on_device < 0 || on_device > 3) return fail(c, SPH_EINVAL, "on_device %d not in 0..3", on_device);
     size_t nf = (size_t)c->scenes[scene].nf;
     if ((st = read_into(c, scene, 100, x, 12 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 101, v, 12 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 102, rho, 4 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 103, pressure, 4 * nf, false, on_device)) != SPH_OK) return st;
-    if (on_device != 2) CK(cudaStreamSynchronize(c->stream));
+    if (on_device <= 1) CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
 
@@ -1313,8 +1315,9 @@ sph_status sph_read_field(sph_ctx *c, int32_t scene, int32_t field, void *out, i
         break;
     default: return fail(c, SPH_EINVAL, "unknown field %d", field);
     }
+    if (on_device < 0 || on_device > 3) return fail(c, SPH_EINVAL, "on_device %d not in 0..3", on_device);
     if ((st = read_into(c, scene, field, out, bytes, boundary, on_device)) != SPH_OK) return st;
-    if (on_device != 2) CK(cudaStreamSynchronize(c->stream));
+    if (on_device <= 1) CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
 }
 

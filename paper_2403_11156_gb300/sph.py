@@ -351,6 +351,19 @@ class Context:
         _check(self.ctx, load().sph_read_state(self.ctx, scene, ptr(x), ptr(v), ptr(rho),
                                                ptr(pressure), 1 if sync else 2))
 
+    def sph_read_state_host(self, scene, x=None, v=None, rho=None, pressure=None, sync=True):
+        """Write into caller-owned host buffers (page-locked torch CPU tensors, numpy arrays
+        or raw pointers); with sync=False the copies are only enqueued on the context's
+        stream (on_device = 3)."""
+        def ptr(t):
+            if t is None:
+                return None
+            if hasattr(t, "data_ptr"):
+                return t.data_ptr()
+            return t.ctypes.data if hasattr(t, "ctypes") else int(t)
+        _check(self.ctx, load().sph_read_state(self.ctx, scene, ptr(x), ptr(v), ptr(rho),
+                                               ptr(pressure), 0 if sync else 3))
+
     def sph_write_state(self, scene=0, x=None, v=None, kappa_prev=None, kappa_v_prev=None):
         def arr(a, shape):
             if a is None:
