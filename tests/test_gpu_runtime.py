@@ -234,3 +234,27 @@ def test_checkpoint_resume_inside_a_batch():
     for u, w in zip(a.sph_read_state(1), b.sph_read_state(1)):
         np.testing.assert_array_equal(u, w)
     np.testing.assert_array_equal(a.sph_read_bodies(1), b.sph_read_bodies(1))
+
+
+def test_read_state_enqueued_into_host_memory():
+    # on_device = 3: the unpermute and the device-to-host copy are only enqueued on the
+    # context's stream; once an event recorded after the call has passed, the page-locked
+    # host buffers hold what the synchronous read returns, for two steps in a row
+    import torch
+    stream = torch.cuda.Stream()
+    g = gpu_ctx(_small(), stream=stream)
+    n = g.n_fluid[0]
+    for _ in range(2):
+        g.sph_step(DT)
+        x = torch.full((n, 3), float("nan"), pin_memory=True)
+        rho = torch.full((n,), float("nan"), pin_memory=True)
+        g.sph_read_state_host(0, x=x, rho=rho, sync=False)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        ev.synchronize()
+        xs, _, rs, _ = g.sph_read_state()
+        np.testing.assert_array_equal(x.numpy(), xs)
+        np.testing.assert_array_equal(rho.numpy(), rs)
+    # an unknown mode is refused
+    st = sph.load().sph_read_state(g.ctx, 0, x.data_ptr(), None, None, None, 4)
+    assert st == sph.SPH_EINVAL
