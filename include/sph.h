@@ -382,6 +382,8 @@ sph_status sph_mlp_train(const float *features, const float *labels, int64_t n, 
 #define SPH_KID_CG_ALPHA 35       /* CG alpha */
 #define SPH_KID_CG_BETA 36        /* CG beta and stopping test */
 #define SPH_KID_BTOUCH 37         /* bodies touched per block (strong) */
+#define SPH_KID_RANK_LARGE_F 38   /* crowded cells of the fluid sort, block-sorted */
+#define SPH_KID_RANK_LARGE_B 39   /* crowded cells of the boundary sort, block-sorted */
 
 /* Device trace for profiling graph replays: with capacity > 0 every kernel's first thread
  * records (globaltimer_ns << 8 | kernel id) in a device ring of that many entries (the
@@ -419,9 +421,10 @@ sph_status sph_launch_count(sph_ctx *ctx, int64_t *out);
  * that array.  The first call on a device looks up the array's device address (with that
  * device current) and should come before any stream capture.  Calls no allocator.
  * Points outside [domain_min, domain_max] (and NaN coordinates) are clamped into the edge
- * cells of the padded grid, as in sph_step.  The order inside a cell is found by counting,
- * per point, the cell's smaller indices, so the work grows with the square of a cell's
- * occupancy: many points clamped into a few cells make the call slow.
+ * cells of the padded grid, as in sph_step.  Inside a cell of up to 64 points the order
+ * comes from counting each point's smaller indices; a more crowded cell is sorted by one
+ * thread block (a stable radix sort on the index), so the work stays linear in n however
+ * the points crowd into cells.
  * SPH_OK means the work was enqueued; whether its prefix scan completed is reported by
  * sph_grid_order_noalloc_status. */
 #define SPH_NOALLOC_MAX_POINTS 262144

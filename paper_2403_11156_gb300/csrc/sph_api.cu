@@ -772,6 +772,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
     ok &= dalloc(c, P.bpos_s, NBa) && dalloc(c, P.bvel_s, NBa) && dalloc(c, P.bid_s, NBa) &&
           dalloc(c, P.bbody_s, NBa);
     ok &= dalloc(c, P.bcell_count, NC) && dalloc(c, P.bcell_start, NC + 1);
+    ok &= dalloc(c, P.large_f, large_capacity(NF)) && dalloc(c, P.large_b, large_capacity(NBa));
     ok &= dalloc(c, P.bkey_tmp, NBa) && dalloc(c, P.bslot_tmp, NBa) && dalloc(c, P.bsid_tmp, NBa) &&
           dalloc(c, P.bsrc_tmp, NBa) && dalloc(c, P.bcell_tmp, NBa);
     ok &= dalloc(c, P.partial, std::max(ntblk, 1));

@@ -2,6 +2,9 @@
 // single-pass decoupled look-back prefix sum (the "prefix sum" of Sec. 5.6), and the
 // stable reorder of every per-particle field into (cell key, particle id) order so that
 // the 27-cell neighbourhood of a particle is 9 contiguous index ranges.
+#include <algorithm>
+
+#include "sph_blocksort.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -26,6 +29,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(Ptrs P)
     const int32_t first = WHAT == SORT_FLUID ? sc.fblk_first : sc.bblk_first;
     const int64_t off = WHAT == SORT_FLUID ? sc.f_off : sc.b_off;
     const int64_t n = WHAT == SORT_FLUID ? sc.nf : sc.nb;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->nlarge[WHAT] = 0;   // this sort's crowded cells
     const int64_t local = (int64_t)(blockIdx.x - first) * kBlock + threadIdx.x;
     if (local >= n) return;
     const int64_t i = off + local;
@@ -60,7 +64,30 @@ __global__ void __launch_bounds__(kBlock) k_scatter(Ptrs P)
     (WHAT == SORT_FLUID ? P.cell_tmp : P.bcell_tmp)[s] = cell;
 }
 
-// 4) rank inside the cell by original id (deterministic (key, id) order) and gather.
+// Copy particle src of the canonical (or original boundary) arrays to sorted slot d.
+template <int WHAT>
+__device__ __forceinline__ void gather_one(const Ptrs &P, uint32_t d, uint32_t src, uint32_t id)
+{
+    if (WHAT == SORT_FLUID) {
+        float4 p = P.pos_c[src];
+        p.w = 0.0f;
+        P.pos_s[d] = p;
+        P.vel_s[d] = P.vel_c[src];
+        P.kprev_s[d] = P.kprev_c[src];
+        P.kvprev_s[d] = P.kvprev_c[src];
+        P.id_s[d] = (int32_t)id;
+    } else {
+        float4 p = P.bx_o[src];
+        p.w = 0.0f;
+        P.bpos_s[d] = p;
+        P.bvel_s[d] = P.bv_o[src];
+        P.bid_s[d] = (int32_t)id;
+        P.bbody_s[d] = P.bbody[src];
+    }
+}
+
+// 4) rank inside the cell by original id (deterministic (key, id) order) and gather.  A
+// cell of more than kRankSmall particles is queued for k_rank_large instead.
 template <int WHAT>
 __global__ void __launch_bounds__(kBlock) k_rank_gather(Ptrs P)
 {
@@ -77,26 +104,39 @@ __global__ void __launch_bounds__(kBlock) k_rank_gather(Ptrs P)
     const uint32_t *start = WHAT == SORT_FLUID ? P.cell_start : P.bcell_start;
     uint32_t cell = (WHAT == SORT_FLUID ? P.cell_tmp : P.bcell_tmp)[s];
     uint32_t b = start[cell], e = start[cell + 1];
+    if (e - b > kRankSmall) {
+        if ((uint32_t)s == b) {
+            const int q = atomicAdd(&P.ctl->nlarge[WHAT], 1);
+            (WHAT == SORT_FLUID ? P.large_f : P.large_b)[q] = cell;
+        }
+        return;
+    }
     uint32_t my = sid[s];
     uint32_t rank = 0;
     for (uint32_t t = b; t < e; ++t) rank += (sid[t] < my) ? 1u : 0u;
-    const uint32_t d = b + rank;
-    const uint32_t src = (WHAT == SORT_FLUID ? P.src_tmp : P.bsrc_tmp)[s];
-    if (WHAT == SORT_FLUID) {
-        float4 p = P.pos_c[src];
-        p.w = 0.0f;
-        P.pos_s[d] = p;
-        P.vel_s[d] = P.vel_c[src];
-        P.kprev_s[d] = P.kprev_c[src];
-        P.kvprev_s[d] = P.kvprev_c[src];
-        P.id_s[d] = (int32_t)my;
-    } else {
-        float4 p = P.bx_o[src];
-        p.w = 0.0f;
-        P.bpos_s[d] = p;
-        P.bvel_s[d] = P.bv_o[src];
-        P.bid_s[d] = (int32_t)my;
-        P.bbody_s[d] = P.bbody[src];
+    gather_one<WHAT>(P, b + rank, (WHAT == SORT_FLUID ? P.src_tmp : P.bsrc_tmp)[s], my);
+}
+
+// 5) the queued crowded cells: each block takes cells of the queue in turn, sorts the
+// cell's (id, source) pairs stably by id and gathers them (the key and slot arrays, free
+// once scattered, are the sort's scratch).  Exits at once when no cell was queued.
+template <int WHAT>
+__global__ void __launch_bounds__(kLargeThreads) k_rank_large(Ptrs P)
+{
+    kernel_enter(P.ctl, (WHAT == SORT_FLUID ? KID_RANK_LARGE_F : KID_RANK_LARGE_B));
+    const int nq = *reinterpret_cast<volatile int32_t *>(&P.ctl->nlarge[WHAT]);
+    const uint32_t *large = WHAT == SORT_FLUID ? P.large_f : P.large_b;
+    const uint32_t *start = WHAT == SORT_FLUID ? P.cell_start : P.bcell_start;
+    uint32_t *sid = WHAT == SORT_FLUID ? P.sid_tmp : P.bsid_tmp;
+    uint32_t *src = WHAT == SORT_FLUID ? P.src_tmp : P.bsrc_tmp;
+    uint32_t *sid2 = WHAT == SORT_FLUID ? P.key_tmp : P.bkey_tmp;
+    uint32_t *src2 = WHAT == SORT_FLUID ? P.slot_tmp : P.bslot_tmp;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const uint32_t cell = large[q];
+        const uint32_t b = start[cell], e = start[cell + 1];
+        block_sort_segment(sid, src, sid2, src2, b, e);
+        for (uint32_t d = b + threadIdx.x; d < e; d += kLargeThreads) gather_one<WHAT>(P, d, src[d], sid[d]);
+        __syncthreads();
     }
 }
 
@@ -223,6 +263,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t *count, uint32_t
 }  // namespace
 
 int32_t scan_tiles_for(int64_t n) { return (int32_t)((n + kScanTile - 1) / kScanTile); }
+int64_t large_capacity(int64_t n) { return n / (kRankSmall + 1) + 1; }
 
 void launch_scan(uint32_t *count, uint32_t *start, int64_t n, uint64_t *status, int32_t tiles,
                  ScanCtl *sc, Control *ctl, cudaStream_t s)
@@ -260,10 +301,15 @@ void launch_scatter(const Ptrs &P, SortWhat what, cudaStream_t s)
 }
 void launch_rank_gather(const Ptrs &P, SortWhat what, cudaStream_t s)
 {
+    // the crowded-cell pass takes as many blocks as cells could be queued, up to one per SM
     if (what == SORT_FLUID) {
-        if (P.nfblk) k_rank_gather<SORT_FLUID><<<P.nfblk, kBlock, 0, s>>>(P);
+        if (P.nfblk) {
+            k_rank_gather<SORT_FLUID><<<P.nfblk, kBlock, 0, s>>>(P);
+            k_rank_large<SORT_FLUID><<<(int)std::min<int64_t>(large_capacity(P.NF), 152), kLargeThreads, 0, s>>>(P);
+        }
     } else if (P.nbblk) {
         k_rank_gather<SORT_BOUNDARY><<<P.nbblk, kBlock, 0, s>>>(P);
+        k_rank_large<SORT_BOUNDARY><<<(int)std::min<int64_t>(large_capacity(P.NB), 152), kLargeThreads, 0, s>>>(P);
     }
 }
 

@@ -114,6 +114,7 @@ struct Control {
     unsigned long long *trace;        // (globaltimer << 8 | kernel id) per launch, or null
     int32_t mlp_n;                    // rows the warm-start network runs on this step
     int32_t pad1;
+    int32_t nlarge[2];                // crowded cells of the fluid (0) / boundary (1) sort
 };
 
 // Kernel identifiers of the device trace.
@@ -154,7 +155,9 @@ enum KernelId : uint32_t {
     KID_CHECK1 = 34,
     KID_CG_ALPHA = 35,
     KID_CG_BETA = 36,
-    KID_BTOUCH = 37
+    KID_BTOUCH = 37,
+    KID_RANK_LARGE_F = 38,
+    KID_RANK_LARGE_B = 39
 };
 
 static_assert(KID_STEP_BEGIN == SPH_KID_STEP_BEGIN, "trace id");
@@ -194,6 +197,8 @@ static_assert(KID_CHECK1 == SPH_KID_CHECK1, "trace id");
 static_assert(KID_CG_ALPHA == SPH_KID_CG_ALPHA, "trace id");
 static_assert(KID_CG_BETA == SPH_KID_CG_BETA, "trace id");
 static_assert(KID_BTOUCH == SPH_KID_BTOUCH, "trace id");
+static_assert(KID_RANK_LARGE_F == SPH_KID_RANK_LARGE_F, "trace id");
+static_assert(KID_RANK_LARGE_B == SPH_KID_RANK_LARGE_B, "trace id");
 
 // First thread of every kernel: count the launch and, when tracing, stamp its start.
 __device__ __forceinline__ void kernel_enter(Control *ctl, uint32_t id)
@@ -244,6 +249,7 @@ struct Ptrs {
     int32_t *bbody_s;
     uint32_t *bcell_count, *bcell_start;
     uint32_t *bkey_tmp, *bslot_tmp, *bsid_tmp, *bsrc_tmp, *bcell_tmp;
+    uint32_t *large_f, *large_b;      // crowded cells of the fluid / boundary sort (lists)
     // reductions
     double *partial;                  // [ntblk] pass A's FP64 error partial per block
     double *partial2;                 // [ntblk] pass B's folds of kFold partials
@@ -317,6 +323,13 @@ void launch_rank_gather(const Ptrs &P, SortWhat what, cudaStream_t s);
 void launch_scan(uint32_t *count, uint32_t *start, int64_t n, uint64_t *status, int32_t tiles,
                  ScanCtl *sc, Control *ctl, cudaStream_t s);
 int32_t scan_tiles_for(int64_t n);
+
+// In-cell ranking: a cell of at most kRankSmall particles ranks each one by counting the
+// cell's smaller ids (O(occupancy) per particle); a more crowded cell is queued and sorted
+// by one block with a stable radix sort (O(occupancy) per pass), so no input makes the
+// grid order quadratic.
+constexpr uint32_t kRankSmall = 64;
+int64_t large_capacity(int64_t n);   // queue entries a sort of n particles can need
 
 // ------------------------------------------------------------------ fluid (sph_fluid.cu)
 void launch_step_begin(const Ptrs &P, cudaStream_t s);

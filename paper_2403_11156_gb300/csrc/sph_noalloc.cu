@@ -6,10 +6,12 @@
 // GPU's memory budget and forbid libraries from allocating, and real-time loops in which
 // an allocation's latency or a possible out-of-memory failure is not acceptable.  For them
 // sph_grid_order_noalloc runs the same counting sort as the per-step neighbour search
-// (cell keys, histogram, decoupled look-back prefix sum, scatter, rank by index) with its
-// scratch in one file-scope static device array of fixed size, which every GPU that loads
-// the library holds until the process exits.
+// (cell keys, histogram, decoupled look-back prefix sum, scatter, rank by index, with the
+// crowded cells sorted by one block each) with its scratch in one file-scope static device
+// array of fixed size, which every GPU that loads the library holds until the process
+// exits.
 #include "sph.h"
+#include "sph_blocksort.cuh"
 #include "sph_internal.cuh"
 
 #include <cmath>
@@ -33,7 +35,9 @@ constexpr size_t kOffSid = kOffSlot + 4 * kMaxPoints;                    // u32 
 constexpr size_t kOffCell = kOffSid + 4 * kMaxPoints;                    // u32 [kMaxPoints]
 constexpr size_t kOffStatus = kOffCell + 4 * kMaxPoints;                 // u64 [kMaxTiles]
 constexpr size_t kOffCtl = kOffStatus + ((8 * kMaxTiles + 255) / 256) * 256;  // Control
-constexpr size_t kScratchBytes = kOffCtl + ((sizeof(Control) + 255) / 256) * 256;
+constexpr int64_t kMaxLarge = kMaxPoints / (kRankSmall + 1) + 1;
+constexpr size_t kOffLarge = kOffCtl + ((sizeof(Control) + 255) / 256) * 256;  // u32 [kMaxLarge]
+constexpr size_t kScratchBytes = kOffLarge + ((4 * kMaxLarge + 255) / 256) * 256;
 
 static __device__ __align__(256) unsigned char g_grid_scratch[kScratchBytes];
 
@@ -41,6 +45,7 @@ struct View {
     uint32_t *count, *start, *key, *slot, *sid, *cell;
     uint64_t *status;
     Control *ctl;
+    uint32_t *large;
 };
 
 View carve(unsigned char *base)
@@ -54,6 +59,7 @@ View carve(unsigned char *base)
     v.cell = reinterpret_cast<uint32_t *>(base + kOffCell);
     v.status = reinterpret_cast<uint64_t *>(base + kOffStatus);
     v.ctl = reinterpret_cast<Control *>(base + kOffCtl);
+    v.large = reinterpret_cast<uint32_t *>(base + kOffLarge);
     return v;
 }
 
@@ -75,6 +81,7 @@ __global__ void k_na_clear(View v, int64_t ncell, int32_t tiles)
         v.ctl->scan[0].done = 0;
         v.ctl->scan[0].epoch = 0;
         v.ctl->error = 0;
+        v.ctl->nlarge[0] = 0;
     }
 }
 
@@ -101,16 +108,36 @@ __global__ void k_na_scatter(View v, int64_t n)
     v.cell[s] = key;
 }
 
+// Rank inside the cell by counting the cell's smaller indices; a cell of more than
+// kRankSmall points is queued for k_na_rank_large instead.
 __global__ void k_na_rank(View v, int64_t n, int32_t *order)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t c = v.cell[s];
     uint32_t b = v.start[c], e = v.start[c + 1];
+    if (e - b > kRankSmall) {
+        if ((uint32_t)s == b) v.large[atomicAdd(&v.ctl->nlarge[0], 1)] = c;
+        return;
+    }
     uint32_t my = v.sid[s];
     uint32_t rank = 0;
     for (uint32_t t = b; t < e; ++t) rank += (v.sid[t] < my) ? 1u : 0u;
     order[b + rank] = (int32_t)my;
+}
+
+// The queued crowded cells: one block per cell at a time sorts the cell's indices stably
+// (the key and slot regions, free once scattered, are its scratch) and writes them out.
+__global__ void __launch_bounds__(kLargeThreads) k_na_rank_large(View v, int32_t *order)
+{
+    const int nq = *reinterpret_cast<volatile int32_t *>(&v.ctl->nlarge[0]);
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const uint32_t c = v.large[q];
+        const uint32_t b = v.start[c], e = v.start[c + 1];
+        block_sort_segment(v.sid, v.cell, v.key, v.slot, b, e);
+        for (uint32_t d = b + threadIdx.x; d < e; d += kLargeThreads) order[d] = (int32_t)v.sid[d];
+        __syncthreads();
+    }
 }
 
 std::mutex g_mu;
@@ -162,6 +189,7 @@ extern "C" sph_status sph_grid_order_noalloc(const float *x, int64_t n, const fl
     launch_scan(v.count, v.start, ncell, v.status, tiles, &v.ctl->scan[0], v.ctl, s);
     k_na_scatter<<<bp, t, 0, s>>>(v, n);
     k_na_rank<<<bp, t, 0, s>>>(v, n, order);
+    k_na_rank_large<<<(int)std::min<int64_t>(n / (kRankSmall + 1) + 1, 152), kLargeThreads, 0, s>>>(v, order);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }
 

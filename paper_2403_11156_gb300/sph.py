@@ -45,7 +45,8 @@ KERNEL_IDS = {i + 1: n for i, n in enumerate([
     "div_pass_b", "dens_pass_b", "div_warm_pass_b", "dens_warm_pass_b", "nonpressure", "warm_density",
     "advect", "step_end", "set_dt", "boundary_update", "boundary_psi", "body_force", "body_reduce",
     "cg_init", "cg_ap", "cg_xr", "cg_p", "mlp_warm", "body_force_inc", "body_apply",
-    "boundary_vel", "div_check", "dens_check", "cg_alpha", "cg_beta", "body_touch"])}
+    "boundary_vel", "div_check", "dens_check", "cg_alpha", "cg_beta", "body_touch",
+    "rank_large_fluid", "rank_large_boundary"])}
 
 
 class SphError(RuntimeError):

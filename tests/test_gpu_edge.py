@@ -87,3 +87,31 @@ def test_one_particle_scene_in_a_batch():
         single.sph_steps(5, DT)
         for u, w in zip(batch.sph_read_state(k), single.sph_read_state()):
             np.testing.assert_array_equal(u, w)
+
+
+@pytest.mark.parametrize("lanes", [1, 8])
+def test_crowded_cells_keep_the_grid_order(lanes):
+    # 1,500 fluid particles squeezed into a few cells (plus a regular block) and 600
+    # boundary points outside the domain, clamped into its edge cells: cells of hundreds of
+    # particles go through the block-sorted path of the grid order, which must still give
+    # the (cell key, id) order bit for bit
+    rng = np.random.default_rng(11)
+    d = scenes.dam_break_small(seed=2, n=(8, 8, 8), box=0.4, lanes_per_particle=lanes,
+                               max_iter_density=1, min_iter_density=1, max_iter_divergence=1)
+    crowd = (0.2 + 0.03 * rng.random((1500, 3))).astype(np.float32)
+    x = np.concatenate([d["fluid_x"], crowd]).astype(np.float32)
+    d["fluid_x"], d["fluid_v"] = x, np.zeros_like(x)
+    out = (np.array([0.9, 0.1, -0.5]) + 0.01 * rng.random((600, 3))).astype(np.float32)
+    bx = np.concatenate([d["boundary_x"], out]).astype(np.float32)
+    d["boundary_x"] = bx
+    d["boundary_body"] = np.full(len(bx), -1, np.int32)
+    g = gpu_ctx(d)
+    g.sph_step(DT)
+    g.sph_synchronize(raise_on_error=False)           # the crowd overflows the lists
+    cell = oracle.default_cell_size(d["radius"])
+    keys = oracle.cell_keys(x, d["domain_min"], d["domain_max"], cell)
+    assert np.bincount(keys).max() > 200               # crowded cells were exercised
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_SORTED_ID), oracle.sort_order(keys))
+    bkeys = oracle.cell_keys(bx, d["domain_min"], d["domain_max"], cell)
+    assert np.bincount(bkeys).max() > 200
+    np.testing.assert_array_equal(g.sph_read_field(sph.FIELD_BOUNDARY_SORTED_ID), oracle.sort_order(bkeys))

@@ -71,3 +71,37 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert sph.sph_grid_order_noalloc(x, too_many, (0, 0, 0), (1, 1, 1), 0.04, out) == sph.SPH_EINVAL
     # 1 m cube at cell 0.004 m: 252^3 cells > SPH_NOALLOC_MAX_CELLS
     assert sph.sph_grid_order_noalloc(x, 4, (0, 0, 0), (1, 1, 1), 0.004, out) == sph.SPH_EINVAL
+
+
+def test_noalloc_crowded_cells_order_and_linear_time():
+    # 5,000 and 20,000 points clamped into at most 8 cells (a corner outside the domain):
+    # the order is the oracle's, and the time grows about linearly with the count (a
+    # per-point count over the whole cell would grow 16-fold from 5k to 20k)
+    import torch
+    dmin, dmax = (0.0, 0.0, 0.0), (0.4, 0.4, 0.4)
+    cell = oracle.default_cell_size(0.01)
+    stream = torch.cuda.current_stream()
+    times = {}
+    for n in (5000, 20000):
+        rng = np.random.default_rng(n)
+        x = (np.array([-1.0, -1.0, -1.0]) + rng.random((n, 3)) * np.array([0.5, 1.6, 1.6]) *
+             np.where(rng.random((n, 3)) < 0.5, 1.0, -1.0)).astype(np.float32)
+        x[:, 1:] = np.clip(x[:, 1:], -2.0, 0.03)       # y, z: first or second cell
+        keys_o = oracle.cell_keys(x, dmin, dmax, cell)
+        assert len(np.unique(keys_o)) <= 8
+        order, keys = _run(x, dmin, dmax, cell, stream)
+        np.testing.assert_array_equal(keys, keys_o)
+        np.testing.assert_array_equal(order, oracle.sort_order(keys_o))
+        xd = torch.from_numpy(x).cuda()
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            sph.sph_grid_order_noalloc(xd, n, dmin, dmax, np.float32(cell), out, None, stream)
+        a.record(stream)
+        for _ in range(10):
+            sph.sph_grid_order_noalloc(xd, n, dmin, dmax, np.float32(cell), out, None, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert sph.sph_grid_order_noalloc_status(stream) == sph.SPH_OK
+        times[n] = a.elapsed_time(b) / 10
+    assert times[20000] < 8.0 * times[5000], times
