@@ -176,26 +176,30 @@ def learned_vs_plain():
     t_train = _t.perf_counter() - t
     out = {"samples": int(f.shape[0]), "data_s": round(t_data, 3), "train_s": round(t_train, 3),
            "train_loss_first": float(hist[0]), "train_loss_last": float(hist[-1])}
+    # the learned start also runs gated: held back (previous-step start instead) in a step
+    # whose previous density solve sat at the 2-iteration floor
     for tag, eta in (("eta_1e-3", 1e-3), ("eta_1e-5", 1e-5)):
         desc = scenes.dam_break_small(eta_density=eta, eta_divergence=eta)
-        out[tag] = warmstart.compare_warm_starts(desc, params, steps=100)
+        out[tag] = warmstart.compare_warm_starts(desc, params, steps=100, gate=2)
     big = scenes.dam_break_rigid()
-    out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(big, params, steps=200)
+    out["dam_break_1.2M_rigid"] = warmstart.compare_warm_starts(big, params, steps=200, gate=2)
     for mode in out["dam_break_1.2M_rigid"].values():
         mode["particle_steps_per_s"] = len(big["fluid_x"]) / (mode["ms_per_step"] / 1000.0)
     for res in (out["eta_1e-3"], out["eta_1e-5"], out["dam_break_1.2M_rigid"]):
         # the solves' iteration floor: at least 2 density and 1 divergence iterations per step
         res["iteration_floor"] = {"density": 2, "divergence": 1}
-        p, l = res["previous"], res["learned"]
-        res["learned_over_previous"] = {
-            "density_iteration_ratio": p["density_iters_per_step"] / l["density_iters_per_step"],
-            "solver_iteration_ratio": (p["density_iters_per_step"] + p["divergence_iters_per_step"]) /
-                                      (l["density_iters_per_step"] + l["divergence_iters_per_step"]),
-            "time_ratio": p["ms_per_step"] / l["ms_per_step"]}
+        p = res["previous"]
+        for key in ("learned", "learned_gated"):
+            l = res[key]
+            res[key + "_over_previous"] = {
+                "density_iteration_ratio": p["density_iters_per_step"] / l["density_iters_per_step"],
+                "solver_iteration_ratio": (p["density_iters_per_step"] + p["divergence_iters_per_step"]) /
+                                          (l["density_iters_per_step"] + l["divergence_iters_per_step"]),
+                "time_ratio": p["ms_per_step"] / l["ms_per_step"]}
     return out, params
 
 
-def learned_headline(desc, params, steps, warmup, autotune, stream):
+def learned_headline(desc, params, steps, warmup, autotune, stream, gate=0):
     """The benchmark workload with the learned warm start, over the same region as the
     plain `value`: `warmup` untimed graph steps from the same initial state, then `steps`
     graph steps timed with CUDA events on the library stream."""
@@ -203,6 +207,7 @@ def learned_headline(desc, params, steps, warmup, autotune, stream):
     from paper_2403_11156_gb300 import scenes, sph
     d = dict(desc)
     d["warm_start"] = scenes.WARM_LEARNED
+    d["learned_gate"] = gate
     n = len(d["fluid_x"])
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with sph.Context(d, stream=stream, autotune=autotune) as g:
@@ -221,7 +226,8 @@ def learned_headline(desc, params, steps, warmup, autotune, stream):
     return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
             "mean_density_iters": (s1["total_dens_iters"] - s0["total_dens_iters"]) / steps,
             "mean_divergence_iters": (s1["total_div_iters"] - s0["total_div_iters"]) / steps,
-            "final_density_error": s1["dens_err"], "status": sph.STATUS_NAMES[status]}
+            "final_density_error": s1["dens_err"], "status": sph.STATUS_NAMES[status],
+            "learned_gate": gate}
 
 
 def batched_learned(params, steps=200):
@@ -231,10 +237,12 @@ def batched_learned(params, steps=200):
     import torch
     from paper_2403_11156_gb300 import scenes, sph
     out = {}
-    for name, mode in (("previous", scenes.WARM_PREVIOUS), ("learned", scenes.WARM_LEARNED)):
+    for name, mode, gate in (("previous", scenes.WARM_PREVIOUS, 0), ("learned", scenes.WARM_LEARNED, 0),
+                             ("learned_gated", scenes.WARM_LEARNED, 2)):
         ds = scenes.batch_dam_break()
         for d in ds:
             d["warm_start"] = mode
+            d["learned_gate"] = gate
         nf = sum(len(d["fluid_x"]) for d in ds)
         stream = torch.cuda.Stream()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -256,6 +264,7 @@ def batched_learned(params, steps=200):
                      "mean_density_iters": float(np.mean(dens)), "max_density_iters": float(np.max(dens)),
                      "mean_divergence_iters": float(np.mean(div))}
     out["time_ratio"] = out["previous"]["ms_per_step"] / out["learned"]["ms_per_step"]
+    out["gated_time_ratio"] = out["previous"]["ms_per_step"] / out["learned_gated"]["ms_per_step"]
     return out
 
 

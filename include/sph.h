@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define SPH_ABI_VERSION 1
+#define SPH_ABI_VERSION 2
 
 typedef enum sph_status {
     SPH_OK = 0,
@@ -136,6 +136,12 @@ typedef struct sph_scene_desc {
     int32_t rigid_coupling;       /* SPH_COUPLING_*                                   */
     float learned_fraction;       /* SPH_WARM_LEARNED: fraction of the network's      */
                                   /* predicted stiffness applied (0..1; 0 = 0.6)      */
+    int32_t learned_gate;         /* SPH_WARM_LEARNED: the network runs in a step     */
+                                  /* only if the scene's previous density solve took  */
+                                  /* more than this many iterations, else the step    */
+                                  /* takes the previous-step warm start (0 = always   */
+                                  /* the network; min_iter_density: skip it while the */
+                                  /* solve sits at its floor)                         */
 } sph_scene_desc;
 
 #define SPH_MAX_BODIES 64

@@ -202,6 +202,7 @@ sph_status validate(sph_ctx *c, const sph_scene_desc &d, int idx)
         return bad("lanes_per_particle (0, 1, 2, 4 or 8)");
     if (!(d.warm_start_fraction >= 0.0f && d.warm_start_fraction <= 1.0f)) return bad("warm_start_fraction (0..1)");
     if (!(d.learned_fraction >= 0.0f && d.learned_fraction <= 1.0f)) return bad("learned_fraction (0..1)");
+    if (d.learned_gate < 0) return bad("learned_gate (>= 0)");
     if (d.rigid_coupling != SPH_COUPLING_WEAK && d.rigid_coupling != SPH_COUPLING_STRONG) return bad("rigid_coupling");
     if (d.pressure_solver != SPH_SOLVER_DFSPH && d.pressure_solver != SPH_SOLVER_WCSPH &&
         d.pressure_solver != SPH_SOLVER_PCISPH)
@@ -686,6 +687,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.pci_c = pci ? (float)pcisph_prototype(d.radius) : 0.0f;
         q.warm_frac = d.warm_start_fraction > 0.0f ? d.warm_start_fraction : 0.5f;
         q.learned_frac = d.learned_fraction > 0.0f ? d.learned_fraction : 0.6f;
+        q.learned_gate = d.learned_gate;
         q.strong = (d.rigid_coupling == SPH_COUPLING_STRONG && d.n_bodies > 0) ? 1 : 0;
         q.has_moving = d.n_bodies > 0 ? 1 : 0;
         q.body_off = nbodies;

@@ -94,6 +94,7 @@ __global__ void k_step_begin(Ptrs P)
     float od = P.ctl->dt_override;
     st.dt = od > 0.0f ? od : (sc.cfl > 0.0f ? st.dt_next : sc.dt_max);
     for (int k = 0; k < 2; ++k) {
+        st.last_it[k] = st.it[k];
         st.it[k] = 0;
         st.err[k] = CUDART_INF;
         st.err0[k] = 0.0;
@@ -628,7 +629,10 @@ __global__ void __launch_bounds__(kBlock) k_nonpressure(Ptrs P)
 // v* gates a fraction (default half) of the previous step's stiffness (kept as kappa
 // dt^2); the learned mode
 // stores the network's input features instead (rho/rho0 - 1, dt Drho/Dt/rho0,
-// (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.
+// (n_f + n_b)/33, kappa_prev/(9.81 h)) and a separate kernel fills kappa0.  With a
+// learned gate g > 0 a scene whose previous density solve took g iterations or fewer
+// takes the previous-step start in this step (the network would run for nothing at the
+// solve's floor).
 template <int T>
 __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
 {
@@ -649,9 +653,11 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     const float dt = c.st->dt;
     const float rho = vi.w;
     const float dev = fmaf(dt, D, rho - sc.rho0);
+    // learned mode (uniform per block): the network runs unless the gate holds it back
+    const bool net = sc.warm == 2 && (sc.learned_gate == 0 || c.st->last_it[1] > sc.learned_gate);
     // learned mode: the gated particles (predicted compression) are appended to the rows
     // of the network kernel, one atomic per warp (the whole warp is converged here)
-    if (sc.warm == 2) {
+    if (net) {
         const bool gated = own && dev > 0.0f && P.ctl->have_mlp;
         const unsigned m = __ballot_sync(0xffffffffu, gated);
         const int lane = threadIdx.x & 31;
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(kBlock) k_warm_density(Ptrs P)
     f.w = P.kprev_s[i] / (dt * dt) / kref;
     reinterpret_cast<float4 *>(P.feat)[i] = f;
     float k0 = 0.0f;
-    if (sc.warm == 1 && dev > 0.0f) k0 = sc.warm_frac * P.kprev_s[i] / (dt * dt);
+    if (!net && dev > 0.0f) k0 = sc.warm_frac * P.kprev_s[i] / (dt * dt);
     // learned mode: zero here, the network kernel fills the gated rows
     P.k0[i] = k0;
     P.ksum[i] = k0;

@@ -57,7 +57,7 @@ struct SceneDev {
     float warm_frac;                  // fraction of the previous stiffness warm-starting a solve
     int32_t strong;                   // strong rigid coupling: bodies pushed during the solves
     float learned_frac;               // fraction of the network's stiffness warm-starting it
-    int32_t pad_l;
+    int32_t learned_gate;             // the network runs only above this many density iterations
 };
 
 // Per-scene mutable state (device).
@@ -76,6 +76,8 @@ struct SceneState {
     double cg_rr, cg_bb, cg_alpha, cg_beta;
     int64_t steps;
     int64_t total_it[2];
+    int32_t last_it[2];               // iterations of the previous step
+    int32_t pad_s[2];
 };
 
 // Rigid body state (device, FP64).

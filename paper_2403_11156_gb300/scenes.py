@@ -34,7 +34,7 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
            xsph_c=0.0, cg_tol=1e-4, cg_max_iter=500, max_fluid_neighbors=0,
            max_boundary_neighbors=0, cell_size=0.0, lanes_per_particle=0, pressure_solver=0,
            eos_stiffness=0.0, eos_exponent=7.0, warm_start_fraction=0.0, rigid_coupling=0,
-           learned_fraction=0.0):
+           learned_fraction=0.0, learned_gate=0):
     return dict(radius=float(radius), rest_density=float(rest_density),
                 viscosity=float(viscosity), gravity=tuple(float(g) for g in gravity),
                 domain_min=tuple(float(a) for a in domain_min),
@@ -52,7 +52,8 @@ def params(radius=0.01, rest_density=1000.0, viscosity=0.01, gravity=(0.0, 0.0, 
                 cell_size=float(cell_size), lanes_per_particle=int(lanes_per_particle),
                 pressure_solver=int(pressure_solver), eos_stiffness=float(eos_stiffness),
                 eos_exponent=float(eos_exponent), warm_start_fraction=float(warm_start_fraction),
-                rigid_coupling=int(rigid_coupling), learned_fraction=float(learned_fraction))
+                rigid_coupling=int(rigid_coupling), learned_fraction=float(learned_fraction),
+                learned_gate=int(learned_gate))
 
 
 def lattice_block(n, spacing, origin, jitter=0.0, rng=None):

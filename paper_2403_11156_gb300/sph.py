@@ -80,7 +80,7 @@ class SceneDesc(C.Structure):
         ("lanes_per_particle", C.c_int32), ("pressure_solver", C.c_int32),
         ("eos_stiffness", C.c_float), ("eos_exponent", C.c_float),
         ("warm_start_fraction", C.c_float), ("rigid_coupling", C.c_int32),
-        ("learned_fraction", C.c_float),
+        ("learned_fraction", C.c_float), ("learned_gate", C.c_int32),
     ]
 
 
@@ -270,6 +270,7 @@ def _make_desc(d, keep):
     s.eos_exponent = d.get("eos_exponent", 7.0)
     s.warm_start_fraction = d.get("warm_start_fraction", 0.0)
     s.learned_fraction = d.get("learned_fraction", 0.0)
+    s.learned_gate = d.get("learned_gate", 0)
     s.rigid_coupling = d.get("rigid_coupling", 0)
     return s
 

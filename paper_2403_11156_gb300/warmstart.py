@@ -82,16 +82,22 @@ def train(features, labels, epochs=30, batch=4096, lr=1e-3, seed=4):
     return params.cpu().numpy(), hist.cpu().numpy()
 
 
-def compare_warm_starts(desc, params, steps=100, warmup=0, dt=0.0):
-    """Step the same scene with the zero, previous-step and learned warm starts; returns
-    per mode: mean density iterations per step, mean first-iteration density error,
-    mean final error, and GPU milliseconds per step (CUDA events, graph replay)."""
+def compare_warm_starts(desc, params, steps=100, warmup=0, dt=0.0, gate=0):
+    """Step the same scene with the zero, previous-step and learned warm starts (and, with
+    gate > 0, the learned start held back while the previous density solve took at most
+    `gate` iterations); returns per mode: mean density iterations per step, mean
+    first-iteration density error, mean final error, and GPU milliseconds per step (CUDA
+    events, graph replay)."""
     import torch
     out = {}
-    for name, mode in (("zero", scenes.WARM_ZERO), ("previous", scenes.WARM_PREVIOUS),
-                       ("learned", scenes.WARM_LEARNED)):
+    modes = [("zero", scenes.WARM_ZERO, 0), ("previous", scenes.WARM_PREVIOUS, 0),
+             ("learned", scenes.WARM_LEARNED, 0)]
+    if gate > 0:
+        modes.append(("learned_gated", scenes.WARM_LEARNED, gate))
+    for name, mode, g_it in modes:
         d = dict(desc)
         d["warm_start"] = mode
+        d["learned_gate"] = g_it
         stream = torch.cuda.Stream()
         with sph.Context(d, stream=stream) as g:
             if mode == scenes.WARM_LEARNED:

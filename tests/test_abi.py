@@ -28,7 +28,7 @@ def test_exports_every_declared_symbol(lib):
     assert "sph_create" in names and "sph_step" in names and "sph_read_state" in names
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.sph_abi_version() == 1
+    assert lib.sph_abi_version() == 2
 
 
 def test_status_strings(lib):

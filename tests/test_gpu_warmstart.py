@@ -146,3 +146,36 @@ def test_trained_network_needs_fewer_iterations():
     learned, previous, zero = (res[m]["density_iters_per_step"] for m in ("learned", "previous", "zero"))
     assert learned <= 0.85 * previous and learned <= 0.6 * zero
     assert res["learned"]["divergence_iters_per_step"] <= 1.1 * res["previous"]["divergence_iters_per_step"]
+
+
+@pytest.mark.parametrize("iters, same_as", [(2, "previous"), (3, "always")])
+def test_learned_gate_selects_the_start(trained, iters, same_as):
+    # learned_gate = 2: a step whose previous density solve took 2 iterations (the floor)
+    # takes the previous-step warm start, one after 3 iterations runs the network.  The
+    # counts are forced; after a first step each run restarts from one common state (the
+    # previous-step run's), so the gated scene's next steps are bit-identical to the
+    # previous-step scene's or to the always-learned scene's
+    params, _ = trained
+    base = forced(scenes.dam_break_small(seed=5, n=(12, 12, 12), box=0.4), 1, iters)
+    specs = (("previous", scenes.WARM_PREVIOUS, 0), ("gated", scenes.WARM_LEARNED, 2),
+             ("always", scenes.WARM_LEARNED, 0))
+    ctxs = {}
+    for name, mode, gate in specs:
+        g = gpu_ctx(dict(base, warm_start=mode, learned_gate=gate))
+        g.sph_set_mlp(params)
+        g.sph_step(4e-4)
+        ctxs[name] = g
+    p = ctxs["previous"]
+    x, v, _, _ = p.sph_read_state()
+    kp, kvp = p.sph_read_field(sph.FIELD_KAPPA_PREV), p.sph_read_field(sph.FIELD_KAPPA_V_PREV)
+    runs = {}
+    for name, g in ctxs.items():
+        g.sph_write_state(0, x, v, kp, kvp)
+        g.sph_steps(3, 4e-4)
+        assert g.sph_synchronize(raise_on_error=False) == sph.SPH_OK
+        xs, vs, _, ps = g.sph_read_state()
+        runs[name] = (xs, vs, ps, g.sph_read_field(sph.FIELD_KAPPA0))
+    other = "always" if same_as == "previous" else "previous"
+    for a, b in zip(runs["gated"], runs[same_as]):
+        np.testing.assert_array_equal(a, b)
+    assert not np.array_equal(runs["gated"][3], runs[other][3])
