@@ -246,7 +246,7 @@ def batched_learned(params, steps=200):
         nf = sum(len(d["fluid_x"]) for d in ds)
         stream = torch.cuda.Stream()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with sph.Context(ds, stream=stream) as g:
+        with sph.Context(ds, stream=stream, autotune=True) as g:
             if mode == scenes.WARM_LEARNED:
                 g.sph_set_mlp(params)
             g.sph_steps(5, 0.0)
@@ -269,8 +269,8 @@ def batched_learned(params, steps=200):
 
 
 def batched_throughput(steps=30, rank=0, world=1, barrier=lambda: None):
-    """64 independent dam breaks (20k-200k particles, log-uniform, seed 5) in one context:
-    every kernel of a step covers all scenes in one launch.  With several GPUs each rank
+    """64 independent dam breaks (20k-200k particles, log-uniform, seed 5) in one autotuned
+    context: every kernel of a step covers all scenes in one launch.  With several GPUs each rank
     steps its share of the scenes (largest first onto the least-loaded rank) and the
     whole-job rate is the sum of particles over the slowest rank's time.  Returns
     particle-steps/s of the batch and, on one GPU, of the same scenes stepped one at a
@@ -284,7 +284,8 @@ def batched_throughput(steps=30, rank=0, world=1, barrier=lambda: None):
     nf = sum(len(d["fluid_x"]) for d in ds)
     stream = torch.cuda.Stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with sph.Context(ds, stream=stream) as g:
+    with sph.Context(ds, stream=stream, autotune=True) as g:
+        tuning = g.sph_get_tuning()
         g.sph_steps(5, 0.0)
         g.sph_synchronize(raise_on_error=False)
         barrier()
@@ -298,6 +299,7 @@ def batched_throughput(steps=30, rank=0, world=1, barrier=lambda: None):
         st = [g.sph_get_stats(k) for k in range(len(ds))]
     ms, nf_all = reduce_timing(ms, nf, world, device="cuda")
     out = {"scenes": len(ds_all), "fluid_particles": int(nf_all), "ranks": world, "ms_per_step": ms,
+           "autotune": {k: tuning[k] for k in ("tuned", "from_cache", "gather_batch", "cell_factor", "lanes")},
            "particle_steps_per_s": nf_all / (ms / 1000.0),
            "density_iters_range": [min(x["dens_iters"] for x in st), max(x["dens_iters"] for x in st)]}
     if world > 1:
