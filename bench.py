@@ -569,13 +569,13 @@ def main():
     # ---- end to end through the C ABI: the same K steps from the same initial state on a
     # second context (same, cached tuning).  Every step is enqueued with its host dt and
     # its result, all positions in original particle order, is read into page-locked host
-    # memory by sph_read_state (on_device = 3: the unpermute and the device-to-host copy
-    # follow the step on the library stream).  The host stays one step ahead: before
-    # reusing a host buffer it waits for the event recorded after the read of two steps
-    # earlier.  The scene is resident on the device (uploaded once at create, outside the
-    # timed region); per step the host supplies dt (4 B) and receives 12 B per particle.
+    # memory by sph_read_state (on_device = 3: unpermuted on the library stream, copied on
+    # the library's copy stream while the next step runs).  The host keeps one read in
+    # flight: after enqueuing step k and its read it waits (sph_read_wait, keep = 1) until
+    # step k - 1's positions are on the host, and it reuses a host buffer only after that.
+    # The scene is resident on the device (uploaded once at create, outside the timed
+    # region); per step the host supplies dt (4 B) and receives 12 B per particle.
     pinned = [torch.empty((n_fluid, 3), dtype=torch.float32, pin_memory=True) for _ in range(2)]
-    done = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = args.steps
     g2 = sph.Context(desc, stream=stream, autotune=not args.no_autotune)
     g2.sph_steps(args.warmup, 0.0)
@@ -584,21 +584,17 @@ def main():
     torch.cuda.synchronize()
     t = time.perf_counter()
     for k in range(e2e_steps):
-        b = k % 2
-        if k >= 2:
-            done[b].synchronize()                   # step k - 2's positions are on the host
         g2.sph_step(0.0)
-        g2.sph_read_state_host(0, x=pinned[b], sync=False)
-        done[b].record(stream)
-    for b in range(2):
-        done[b].synchronize()
+        g2.sph_read_state_host(0, x=pinned[k % 2], sync=False)
+        g2.sph_read_wait(1)                         # step k - 1's positions are on the host
+    g2.sph_read_wait(0)
     e2e_wall = time.perf_counter() - t
     x_e2e = pinned[(e2e_steps - 1) % 2].numpy().copy()
     g2.close()
     e2e_ms, e2e_units = reduce_timing(e2e_wall * 1000.0, n_fluid * e2e_steps, world, device="cuda")
     e2e = {"value": e2e_units / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 4,
            "d2h_bytes_per_step": 12 * n_fluid,
-           "path": "sph_step + sph_read_state(on_device = 3) into page-locked host memory",
+           "path": "sph_step + sph_read_state(on_device = 3) into page-locked host memory, sph_read_wait(keep = 1)",
            "last_positions_finite": bool(np.all(np.isfinite(x_e2e)))}
 
     # ---- kernel breakdown: eager steps with CUDA events around every launch (graph kernel

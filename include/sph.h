@@ -217,13 +217,20 @@ sph_status sph_synchronize(sph_ctx *ctx);
  * step).  on_device == 0: host memory, synchronises; 1: device memory, synchronises;
  * 2: device memory, only enqueued on the context's stream (order later work after it with
  * an event on that stream), so a caller can copy a step's result out while the next step
- * runs; 3: host memory, only enqueued (the device-to-host copies follow the step on the
- * context's stream: with page-locked host buffers the call returns at once and the data
- * is there once the stream has passed this point, which an event recorded on the stream
- * after the call or sph_synchronize tells; with pageable buffers the copies wait for the
- * stream).  Other values: SPH_EINVAL. */
+ * runs; 3: host memory, only enqueued: the fields are unpermuted on the context's stream
+ * into one of two library staging slots, and a copy stream of the library moves them to
+ * the host while later steps run.  With page-locked host buffers the call returns at
+ * once; the data is there once sph_read_wait (or sph_synchronize) says so.  With pageable
+ * buffers the copy waits for the step.  Other values: SPH_EINVAL. */
 sph_status sph_read_state(sph_ctx *ctx, int32_t scene, float *x, float *v, float *rho,
                           float *pressure, int32_t on_device);
+
+/* Wait until at most `keep` of the host reads enqueued with on_device = 3 (sph_read_state
+ * or sph_read_field) are still in flight; reads complete in the order they were enqueued.
+ * keep = 0 waits for all of them.  keep: 0..7, else SPH_EINVAL.  A caller stepping and
+ * reading every step can keep one read in flight (keep = 1) so that each step's copy
+ * overlaps the next step. */
+sph_status sph_read_wait(sph_ctx *ctx, int32_t keep);
 
 /* Overwrite the dynamic state of one scene (checkpoint restore); NULL keeps a field.
  * kappa_prev = previous step's total density stiffness times dt^2, kappa_v_prev =

@@ -110,6 +110,17 @@ struct sph_ctx {
     int batch = 4;                       // neighbours in flight per thread in the Jacobi passes
     sph_tuning tuning{};
     uint32_t *h_flag = nullptr;          // pinned word for eager loop control
+
+    // enqueued host reads (on_device = 3): the unpermuted fields go to one of two device
+    // staging slots on the context stream, and a copy stream moves them to the host while
+    // later work runs; every read records a completion event in a ring
+    static constexpr int kReadRing = 8;
+    cudaStream_t copy = nullptr;
+    void *stage[2] = {nullptr, nullptr};
+    size_t stage_bytes[2] = {0, 0};
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    cudaEvent_t read_done[kReadRing] = {};
+    int64_t reads = 0;                   // host reads enqueued so far
 };
 
 namespace {
@@ -1227,6 +1238,7 @@ sph_status sph_synchronize(sph_ctx *c)
     sph_status st = check_ctx(c);
     if (st != SPH_OK) return st;
     CK(cudaStreamSynchronize(c->stream));
+    if (c->copy) CK(cudaStreamSynchronize(c->copy));
     Control hctl;
     CK(cudaMemcpy(&hctl, c->P.ctl, sizeof hctl, cudaMemcpyDeviceToHost));
     if (hctl.error)
@@ -1246,11 +1258,80 @@ sph_status sph_synchronize(sph_ctx *c)
     return result;
 }
 
+sph_status sph_read_wait(sph_ctx *c, int32_t keep)
+{
+    sph_status st = check_ctx(c);
+    if (st != SPH_OK) return st;
+    if (keep < 0 || keep >= sph_ctx::kReadRing) return fail(c, SPH_EINVAL, "keep %d not in 0..%d", keep,
+                                                             sph_ctx::kReadRing - 1);
+    const int64_t last = c->reads - 1 - keep;   // the newest read that must be complete
+    if (last >= 0) CK(cudaEventSynchronize(c->read_done[last % sph_ctx::kReadRing]));
+    return SPH_OK;
+}
+
 static sph_status scene_ok(sph_ctx *c, int32_t scene)
 {
     sph_status st = check_ctx(c);
     if (st != SPH_OK) return st;
     if (scene < 0 || scene >= c->nscenes) return fail(c, SPH_EINVAL, "scene index %d out of range", scene);
+    return SPH_OK;
+}
+
+// One enqueued host read (on_device = 3) of several fields of one scene: each field's
+// unpermute kernel writes its slice of a staging slot on the context stream, then the copy
+// stream copies the slot to the caller's host buffers and records the read's completion
+// event.  A slot is refilled only after the read that last used it (two reads back) has
+// been copied out.
+struct HostField {
+    int field;
+    void *out;
+    size_t bytes;
+    bool boundary;
+};
+static sph_status read_host_async(sph_ctx *c, int32_t scene, const HostField *f, int nf)
+{
+    size_t total = 0;
+    for (int k = 0; k < nf; ++k)
+        if (f[k].out) total += (f[k].bytes + 255) & ~size_t(255);
+    if (total == 0) return SPH_OK;
+    if (!c->copy) {
+        CK(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&c->staged[k], cudaEventDisableTiming));
+        for (int k = 0; k < sph_ctx::kReadRing; ++k) CK(cudaEventCreateWithFlags(&c->read_done[k], cudaEventDisableTiming));
+    }
+    const int slot = (int)(c->reads & 1);
+    if (c->reads >= 2) CK(cudaStreamWaitEvent(c->stream, c->read_done[(c->reads - 2) % sph_ctx::kReadRing], 0));
+    if (c->stage_bytes[slot] < total) {
+        void *p = dev_alloc(c, total);
+        if (!p) return fail(c, SPH_ENOMEM, "host read staging (%zu bytes)", total);
+        c->stage[slot] = p;
+        c->stage_bytes[slot] = total;
+    }
+    const SceneDev &q = c->scenes[scene];
+    unsigned char *base = static_cast<unsigned char *>(c->stage[slot]);
+    size_t off = 0;
+    for (int k = 0; k < nf; ++k) {
+        if (!f[k].out) continue;
+        const int64_t n = f[k].boundary ? q.nb : q.nf;
+        if (n > 0) {
+            const int blocks = (int)((n + 255) / 256);
+            if (f[k].boundary) k_read_boundary<<<blocks, 256, 0, c->stream>>>(c->P, scene, f[k].field, base + off);
+            else k_read_fluid<<<blocks, 256, 0, c->stream>>>(c->P, scene, f[k].field, base + off);
+        }
+        off += (f[k].bytes + 255) & ~size_t(255);
+    }
+    sph_status st = check_async(c);
+    if (st != SPH_OK) return st;
+    CK(cudaEventRecord(c->staged[slot], c->stream));
+    CK(cudaStreamWaitEvent(c->copy, c->staged[slot], 0));
+    off = 0;
+    for (int k = 0; k < nf; ++k) {
+        if (!f[k].out) continue;
+        if (f[k].bytes) CK(cudaMemcpyAsync(f[k].out, base + off, f[k].bytes, cudaMemcpyDeviceToHost, c->copy));
+        off += (f[k].bytes + 255) & ~size_t(255);
+    }
+    CK(cudaEventRecord(c->read_done[c->reads % sph_ctx::kReadRing], c->copy));
+    c->reads += 1;
     return SPH_OK;
 }
 
@@ -1287,6 +1368,11 @@ sph_status sph_read_state(sph_ctx *c, int32_t scene, float *x, float *v, float *
     if (st != SPH_OK) return st;
     if (on_device < 0 || on_device > 3) return fail(c, SPH_EINVAL, "on_device %d not in 0..3", on_device);
     size_t nf = (size_t)c->scenes[scene].nf;
+    if (on_device == 3) {
+        const HostField f[4] = {{100, x, 12 * nf, false}, {101, v, 12 * nf, false}, {102, rho, 4 * nf, false},
+                                {103, pressure, 4 * nf, false}};
+        return read_host_async(c, scene, f, 4);
+    }
     if ((st = read_into(c, scene, 100, x, 12 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 101, v, 12 * nf, false, on_device)) != SPH_OK) return st;
     if ((st = read_into(c, scene, 102, rho, 4 * nf, false, on_device)) != SPH_OK) return st;
@@ -1319,6 +1405,10 @@ sph_status sph_read_field(sph_ctx *c, int32_t scene, int32_t field, void *out, i
     default: return fail(c, SPH_EINVAL, "unknown field %d", field);
     }
     if (on_device < 0 || on_device > 3) return fail(c, SPH_EINVAL, "on_device %d not in 0..3", on_device);
+    if (on_device == 3) {
+        const HostField f[1] = {{field, out, bytes, boundary}};
+        return read_host_async(c, scene, f, 1);
+    }
     if ((st = read_into(c, scene, field, out, bytes, boundary, on_device)) != SPH_OK) return st;
     if (on_device <= 1) CK(cudaStreamSynchronize(c->stream));
     return SPH_OK;
@@ -1573,6 +1663,14 @@ void sph_destroy(sph_ctx *c)
 {
     if (!c) return;
     if (c->stream || true) cudaStreamSynchronize(c->stream);
+    if (c->copy) {
+        cudaStreamSynchronize(c->copy);
+        cudaStreamDestroy(c->copy);
+        for (auto e : c->staged)
+            if (e) cudaEventDestroy(e);
+        for (auto e : c->read_done)
+            if (e) cudaEventDestroy(e);
+    }
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);

@@ -161,6 +161,7 @@ def load():
     L.sph_destroy.argtypes = [vp]
     L.sph_grid_order_noalloc.argtypes = [vp, C.c_int64, fp, fp, C.c_float, vp, vp, vp]
     L.sph_grid_order_noalloc_status.argtypes = [vp]
+    L.sph_read_wait.argtypes = [vp, ip]
     L.sph_set_mlp.argtypes = [vp, fp, C.c_int64]
     L.sph_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.sph_set_trace.argtypes = [vp, ip]
@@ -175,7 +176,7 @@ def load():
     for name in ("sph_create", "sph_create_batch", "sph_step", "sph_steps", "sph_synchronize",
                  "sph_read_state", "sph_write_state", "sph_read_field", "sph_get_stats", "sph_probe_wait_timeout",
                  "sph_read_bodies", "sph_set_mode", "sph_kernel_times", "sph_launch_count",
-                 "sph_grid_order_noalloc", "sph_grid_order_noalloc_status", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
+                 "sph_grid_order_noalloc", "sph_grid_order_noalloc_status", "sph_read_wait", "sph_set_mlp", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train", "sph_get_tuning", "sph_set_trace",
                  "sph_read_trace", "sph_surface_field", "sph_surface_mesh", "sph_render_heightmap"):
         getattr(L, name).restype = C.c_int32
     _lib = L
@@ -353,10 +354,14 @@ class Context:
         _check(self.ctx, load().sph_read_state(self.ctx, scene, ptr(x), ptr(v), ptr(rho),
                                                ptr(pressure), 1 if sync else 2))
 
+    def sph_read_wait(self, keep=0):
+        """Wait until at most `keep` enqueued host reads are still in flight."""
+        _check(self.ctx, load().sph_read_wait(self.ctx, int(keep)))
+
     def sph_read_state_host(self, scene, x=None, v=None, rho=None, pressure=None, sync=True):
         """Write into caller-owned host buffers (page-locked torch CPU tensors, numpy arrays
-        or raw pointers); with sync=False the copies are only enqueued on the context's
-        stream (on_device = 3)."""
+        or raw pointers); with sync=False the read is only enqueued (on_device = 3) and its
+        data is there once sph_read_wait says so."""
         def ptr(t):
             if t is None:
                 return None

@@ -237,24 +237,35 @@ def test_checkpoint_resume_inside_a_batch():
 
 
 def test_read_state_enqueued_into_host_memory():
-    # on_device = 3: the unpermute and the device-to-host copy are only enqueued on the
-    # context's stream; once an event recorded after the call has passed, the page-locked
-    # host buffers hold what the synchronous read returns, for two steps in a row
+    # on_device = 3: the read is only enqueued (unpermute on the context stream, copy on the
+    # library's copy stream); once sph_read_wait says so, the page-locked host buffers hold
+    # what the synchronous read returns.  Reads stay in flight across the next step: the
+    # buffers of step k are checked after step k + 1 was enqueued (keep = 1 each step).
     import torch
     stream = torch.cuda.Stream()
     g = gpu_ctx(_small(), stream=stream)
     n = g.n_fluid[0]
-    for _ in range(2):
+    bufs = [(torch.full((n, 3), float("nan"), pin_memory=True), torch.full((n,), float("nan"), pin_memory=True))
+            for _ in range(2)]
+    ref = []
+    with sph.Context(_small(), stream=torch.cuda.Stream()) as h:
+        for _ in range(4):
+            h.sph_step(DT)
+            xs, _, rs, _ = h.sph_read_state()
+            ref.append((xs, rs))
+    for k in range(4):
         g.sph_step(DT)
-        x = torch.full((n, 3), float("nan"), pin_memory=True)
-        rho = torch.full((n,), float("nan"), pin_memory=True)
+        x, rho = bufs[k % 2]
         g.sph_read_state_host(0, x=x, rho=rho, sync=False)
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        ev.synchronize()
-        xs, _, rs, _ = g.sph_read_state()
-        np.testing.assert_array_equal(x.numpy(), xs)
-        np.testing.assert_array_equal(rho.numpy(), rs)
-    # an unknown mode is refused
-    st = sph.load().sph_read_state(g.ctx, 0, x.data_ptr(), None, None, None, 4)
+        g.sph_read_wait(1)                            # step k - 1's read is on the host
+        if k >= 1:
+            xp, rp = bufs[(k - 1) % 2]
+            np.testing.assert_array_equal(xp.numpy(), ref[k - 1][0])
+            np.testing.assert_array_equal(rp.numpy(), ref[k - 1][1])
+    g.sph_read_wait(0)
+    np.testing.assert_array_equal(bufs[1][0].numpy(), ref[3][0])
+    np.testing.assert_array_equal(bufs[1][1].numpy(), ref[3][1])
+    # an unknown mode and a keep beyond the ring are refused
+    st = sph.load().sph_read_state(g.ctx, 0, bufs[0][0].data_ptr(), None, None, None, 4)
     assert st == sph.SPH_EINVAL
+    assert sph.load().sph_read_wait(g.ctx, 8) == sph.SPH_EINVAL
