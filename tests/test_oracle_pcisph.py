@@ -1,6 +1,6 @@
 """Pins of the oracle's PCISPH solve (an iterative PPE solver of Alg. ppe_solver, the
 predictive-corrective form the paper cites): the prototype stiffness against a direct
-lattice sum, monotone convergence with the iteration count, the 0.1 % tolerance over a dam
+lattice sum, its closed form, and half the DFSPH factor of the prototype particle, monotone convergence with the iteration count, the 0.1 % tolerance over a dam
 break, momentum conservation of the pressure forces, and hydrostatic equilibrium (the
 walls carry the fluid's weight)."""
 import math
@@ -29,6 +29,29 @@ def test_prototype_factor_lattice_sum():
     m_over_rho0 = s ** 3
     want = 1.0 / (2.0 * m_over_rho0 ** 2 * tot)
     assert o.pcisph_factor() == pytest.approx(want, rel=1e-12)
+    # closed form: the shells of the lattice at q = 1/2 (6, g = -1/4), sqrt2/2 (12) and
+    # sqrt3/2 (8, g = -(1 - q)^2); the six at q = 1 have g = 0 and sum grad W = 0 by symmetry
+    G = 6 / 16 + 12 * (1 - math.sqrt(2) / 2) ** 4 + 8 * (1 - math.sqrt(3) / 2) ** 4
+    closed = 1.0 / (2.0 * s ** 6 * (48.0 / (math.pi * h ** 4)) ** 2 * G)
+    assert o.pcisph_factor() == pytest.approx(closed, rel=1e-12)
+
+
+def test_prototype_factor_is_half_the_dfsph_factor_of_the_prototype(oracle_lib):
+    # PCISPH's stiffness assumes every neighbour carries the same pressure correction, so its
+    # update moves the prototype particle twice as far as DFSPH's exact one-particle factor:
+    # p = delta (rho* - rho0)/dt^2 and kappa = alpha (rho* - rho0)/dt^2 with p = kappa rho give
+    # delta = alpha rho0^2 / (2 rho) on the interior of the full lattice (alpha pinned in
+    # test_oracle_alpha.py)
+    r = 2.0 ** -7
+    x = scenes.lattice_block((9, 9, 9), 2 * r, (0.25, 0.25, 0.25))
+    d = scenes.random_cloud(1, radius=r, extent=0.6, max_iter_density=0, max_iter_divergence=0,
+                            warm_start=0, divergence_solve=0, viscosity_mode=0, gravity=(0.0, 0.0, 0.0))
+    d["fluid_x"], d["fluid_v"] = x, np.zeros_like(x)
+    o = oracle_lib.Scene(d)
+    o.step(1e-4)
+    centre = 4 + 9 * (4 + 9 * 4)
+    alpha, rho = o.get(oracle_lib.ALPHA)[centre], o.get(oracle_lib.RHO)[centre]
+    assert o.pcisph_factor() == pytest.approx(alpha * 1000.0 ** 2 / (2.0 * rho), rel=1e-12)
 
 
 def test_pcisph_converges_with_iterations():
