@@ -21,7 +21,7 @@
  * and pressure-acceleration building blocks.
  *
  * Pins (see tests/test_oracle_*.py): kernel normalisation and gradient antisymmetry,
- * lattice rest density, the DFSPH factor alpha (closed-form lattice value, and the exact
+ * lattice rest density, the boundary pseudo-mass of a flat wall lattice, the DFSPH factor alpha (closed-form lattice value, and the exact
  * cancellation of a lone compression next to a wall by one Jacobi update), brute-force
  * neighbour sets, momentum antisymmetry of pressure, viscosity and boundary forces,
  * hydrostatic pressure in a resting tank (weight on the walls, interior gradient within

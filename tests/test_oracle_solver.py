@@ -4,7 +4,8 @@ Rest density on a full lattice (closed form), momentum antisymmetry of the press
 acceleration (Sec. 3.3 Eq. pressure_acceleration), zero modes and dissipation of the
 explicit viscosity (Sec. 3.6.1 Eq. lap), convergence of the Jacobi PPE loop (Alg.
 ppe_solver), hydrostatic equilibrium in a resting tank (force balance and a 5 % interior
-pressure gradient), bookkeeping of the Akinci boundary impulse (Sec. 3.5), mass conservation.
+pressure gradient), bookkeeping of the Akinci boundary impulse (Sec. 3.5), the boundary
+pseudo-mass of a flat wall lattice in closed form, mass conservation.
 """
 import math
 
@@ -209,3 +210,28 @@ def test_boundary_impulse_bookkeeping(oracle_lib):
         imp = s.get(oracle_lib.FB_IMPULSE).sum(0)
         assert np.abs(imp).max() > 1e-6
         np.testing.assert_allclose(dp, imp, rtol=1e-9, atol=1e-12 * np.abs(imp).max())
+
+
+def test_boundary_pseudo_mass_of_a_flat_wall(oracle_lib):
+    # Psi_b = rho0 / sum_k W_bk over the boundary particles within h (Sec. 3.5), the particle
+    # itself included.  On a flat square lattice of spacing h/2 (exact in float) an interior
+    # wall particle sees itself, 4 neighbours at q = 1/2 (w = 1/4) and 4 at q = sqrt2/2
+    # (w = 2 (1 - sqrt2/2)^3); the 4 at q = 1 have W = 0.  So
+    #   Psi = rho0 / (sigma (2 + 8 (1 - sqrt2/2)^3)),  sigma = 8 / (pi h^3).
+    r = 2.0 ** -7
+    h = 4 * r
+    wall = scenes.plane((20, 20), 2 * r, (0.25, 0.25, 0.25))
+    d = scenes.random_cloud(1, radius=r, extent=0.6, **_quiet())
+    d["fluid_x"] = np.array([[0.05, 0.05, 0.05]], np.float32)
+    d["fluid_v"] = np.zeros_like(d["fluid_x"])
+    d["boundary_x"] = wall
+    d["boundary_body"] = np.full(len(wall), -1, np.int32)
+    s = oracle_lib.Scene(d)
+    s.prepare()
+    psi = s.get(oracle_lib.PSI)
+    centre = 10 + 21 * 10
+    sigma = 8.0 / (math.pi * h ** 3)
+    want = 1000.0 / (sigma * (2.0 + 8.0 * (1.0 - math.sqrt(2.0) / 2.0) ** 3))
+    assert psi[centre] == pytest.approx(want, rel=1e-12)
+    # a corner particle has fewer neighbours, so a larger pseudo-mass
+    assert psi[0] > psi[centre]
