@@ -14,7 +14,10 @@ particle's predicted density error exactly, so two independent checks pin it:
   rounding.  The test recomputes rho*_i from the oracle's output velocities with
   brute-force neighbours (Eq. density_source with the SPH divergence), so a wrong alpha
   (a dropped S2, Psi moved into S2 or left out of S1, m squared once too often) leaves a
-  residual of the same order as the initial error.
+  residual of the same order as the initial error;
+* the same property in the divergence-free solve (Eq. velocity_source): one particle moving
+  towards the floor among resting fluid gets kappa_v = alpha D rho/Dt / dt, and one update
+  brings its D rho/Dt to zero to rounding.
 """
 import math
 
@@ -103,3 +106,47 @@ def test_alpha_cancels_a_lone_compression_next_to_a_wall(oracle_lib, drop):
     # the wall is a large part of S1 (so the pin covers the boundary reading of alpha)
     assert np.linalg.norm(s1b) > 0.3 * np.linalg.norm(s1f + s1b)
     assert abs(rs - 1000.0) <= 1e-9 * e0
+
+
+def _drho_dt(oracle_lib, xf, v, psi, xb, i, h, m):
+    """SPH rate of density change (continuity equation with the Sec. 3.2 divergence and the
+    Sec. 3.5 boundary term, walls at rest) of particle i, brute-force neighbours."""
+    h2 = np.float32(h) * np.float32(h)
+
+    def within(Y):
+        dd = (xf[i][None, :] - Y).astype(np.float32)
+        d2 = (dd[:, 0] * dd[:, 0] + dd[:, 1] * dd[:, 1]) + dd[:, 2] * dd[:, 2]
+        return np.nonzero(d2 < h2)[0]
+
+    xi = xf[i].astype(np.float64)
+    s = 0.0
+    for j in within(xf):
+        if j != i:
+            s += m * np.dot(v[i] - v[j], oracle_lib.gradW(xi - xf[j].astype(np.float64), h))
+    for b in within(xb):
+        s += psi[b] * np.dot(v[i], oracle_lib.gradW(xi - xb[b].astype(np.float64), h))
+    return s
+
+
+def test_alpha_cancels_a_lone_divergence_next_to_a_wall(oracle_lib):
+    # the divergence-free solve (Eq. velocity_source) uses the same factor: with one particle
+    # moving towards the floor among resting fluid, kappa_v = alpha D rho/Dt / dt, and one
+    # update of Eq. pressure_acceleration brings its D rho/Dt to zero to rounding
+    rr, dt = 0.01, 4e-4
+    x = scenes.lattice_block((6, 6, 4), 2 * rr * 1.06, (0.05, 0.05, scenes.WALL_GAP * 2 * rr))
+    i = 2 + 6 * 2
+    v = np.zeros_like(x)
+    v[i] = (0.0, 0.0, -0.5)
+    d = scenes.dam_break_small(seed=1, n=(2, 2, 2), box=0.3,
+                               **_quiet(divergence_solve=1, min_iter_divergence=1, max_iter_divergence=1))
+    d["fluid_x"], d["fluid_v"] = x, v
+    s = oracle_lib.Scene(d)
+    s.step(dt)
+    psi, xb, m = s.get(oracle_lib.PSI), d["boundary_x"], s.mass
+    v0 = v.astype(np.float64)
+    # only particle i converges on its neighbours, so only its kappa_v is non-zero
+    rates = [_drho_dt(oracle_lib, x, v0, psi, xb, k, 4 * rr, m) for k in range(len(x))]
+    assert [k for k, r in enumerate(rates) if r > 0.0] == [i]
+    assert s.stats()["div_iters"] == 1
+    after = _drho_dt(oracle_lib, x, s.get(oracle_lib.V_DIV), psi, xb, i, 4 * rr, m)
+    assert abs(after) <= 1e-9 * rates[i]
