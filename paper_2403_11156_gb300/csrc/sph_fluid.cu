@@ -438,9 +438,14 @@ __global__ void __launch_bounds__(kBlock) k_pass_a(Ptrs P)
 // pressure_acceleration with p/rho^2 = kappa/rho, plus the boundary term of Sec. 3.5
 // Eq. rigid_pressure per unit fluid mass:
 //   v_i -= dt [ sum_j m (k_i/rho_i + k_j/rho_j) grad W_ij + sum_b Psi_b (k_i/rho_i) grad W_ib ]
-// WARM = 1 applies the warm-start kappas (no loop bookkeeping).
+// WARM = 1 applies the warm-start kappas (no loop bookkeeping).  With one lane and gather
+// batch 4 the loop's pass B is held to 40 registers (12 resident blocks per SM instead of
+// 10): it is bound by the gathers' latency, and the extra warps outweigh a few spilled words
+// (measured on the 1.2M scene: 84 -> 80 us per density launch, 90 -> 81 per divergence
+// launch).  Every other variant keeps the compiler's choice (a minimum of 0 blocks): the warm
+// pass already fits in 40 registers, and batch 8 would spill 152 bytes.
 template <int S, int WARM, int B, int T>
-__global__ void __launch_bounds__(kBlock) k_pass_b(Ptrs P)
+__global__ void __launch_bounds__(kBlock, (T == 1 && WARM == 0 && B == 4) ? 11 : 0) k_pass_b(Ptrs P)
 {
     kernel_enter(P.ctl, (WARM ? KID_PASS_B0W + S : KID_PASS_B0 + S));
     const Lane<T> c = lane_ctx<T>(P);
