@@ -7,7 +7,9 @@ equal, the tolerances of the small-scene parity tests), the learned warm start's
 every particle against the oracle's FP64 network, and solver invariants over 20 steps.  The
 64-scene batch (5.07M particles in one context) and the 250k-particle implicit-viscosity
 column are checked in their benchmark configurations too: the batch's smallest and largest
-scenes field by field, the column's CG velocity against the oracle's FP64 system."""
+scenes field by field, the column's CG velocity against the oracle's FP64 system.  WCSPH,
+PCISPH and strong coupling each take one step on the 1.2M dam break from the GPU's state,
+compared with the oracle field by field."""
 import numpy as np
 import pytest
 
@@ -235,6 +237,37 @@ def test_wcsph_step_full():
     tol = 1e-3 * np.abs(dv).max() + 1e-5 * np.abs(o.get(oracle.V)).max()
     assert np.abs(v2 - o.get(oracle.V)).max() <= tol
     assert np.abs(x2 - o.get(oracle.X)).max() <= tol * dt + 1e-6
+
+
+def test_pcisph_step_full():
+    # the 1.2M dam break (no boxes) under PCISPH: 10 steps build a compressed state, then one
+    # step from the GPU's state on both sides with three refinements forced, at the
+    # tolerances of the small-scene PCISPH parity test (pressure: 3 refinements of delta times
+    # the FP32 density resolution 1e-5 rho0; velocities: 2e-3 of the pressure velocity change)
+    d = forced(scenes.dam_break_rigid(n_boxes=0, pressure_solver=scenes.SOLVER_PCISPH,
+                                      warm_start=scenes.WARM_ZERO, divergence_solve=0), 0, 3)
+    g = gpu_ctx(d)
+    g.sph_steps(10, DT)
+    x, v, _, _ = g.sph_read_state()
+    o = oracle.Scene(d)
+    z = np.zeros(len(x), np.float32)
+    o.set_state(x, v, z, z)
+    g.sph_step(DT)
+    g.sph_synchronize(raise_on_error=False)
+    o.step(DT)
+    assert_rel(g.sph_read_field(sph.FIELD_RHO), o.get(oracle.RHO), 1e-5, what="rho")
+    x2, v2, _, p2 = g.sph_read_state()
+    p_ref = o.get(oracle.PRESSURE)
+    delta = o.pcisph_factor() / DT ** 2
+    assert p_ref.max() > 0
+    assert np.abs(p2 - p_ref).max() <= 3 * delta * 1e-5 * d["rest_density"] + 1e-5 * np.abs(p_ref).max()
+    dv = o.get(oracle.V) - o.get(oracle.V_NONP)
+    tol = 2e-3 * np.abs(dv).max() + 1e-5 * np.abs(o.get(oracle.V)).max()
+    assert np.abs(v2 - o.get(oracle.V)).max() <= tol
+    assert np.abs(x2 - o.get(oracle.X)).max() <= tol * DT + 1e-6
+    gs, os_ = g.sph_get_stats(), o.stats()
+    assert gs["dens_iters"] == os_["dens_iters"] == 3 and gs["div_iters"] == 0
+    assert gs["dens_err"] == pytest.approx(os_["dens_err"], rel=2e-3, abs=1e-7)
 
 
 def test_strong_coupling_step_full():
