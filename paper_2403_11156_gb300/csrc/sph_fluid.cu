@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P
         P.kvsum[i] = kv0;
         set_w(P.pos_s, i, kv0 / rho);
     }
-    // the counts are the same in all lanes of a particle
+    // the counts are the same in all lanes of a particle (one atomic per warp: spread over
+    // this long sweep they cost less than a block barrier would)
     const int mf = warp_max(nn_f), mb = warp_max(nn_b);
     if ((threadIdx.x & 31) == 0) {
         if (mf > 0) atomicMax(&c.st->max_nn_f, mf);
@@ -719,10 +720,25 @@ __global__ void __launch_bounds__(kBlock) k_advect(Ptrs P)
     float m = v2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    // the block's largest finite |v|^2 and its bad flag reach the scene with one atomic each
+    // (one per warp, on a single word, serialises in L2 and bounded this kernel)
+    __shared__ float s_m[kBlock / 32];
+    __shared__ unsigned s_bad[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {
-        if (m > 0.0f && isfinite(m)) atomicMax(reinterpret_cast<int *>(&c.st->maxv2), __float_as_int(m));
-        if (anybad) atomicOr(&c.st->flags, 4);
+        s_m[threadIdx.x >> 5] = (m > 0.0f && isfinite(m)) ? m : 0.0f;
+        s_bad[threadIdx.x >> 5] = anybad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bm = s_m[0];
+        unsigned bb = s_bad[0];
+        for (int w = 1; w < kBlock / 32; ++w) {
+            bm = fmaxf(bm, s_m[w]);
+            bb |= s_bad[w];
+        }
+        if (bm > 0.0f) atomicMax(reinterpret_cast<int *>(&c.st->maxv2), __float_as_int(bm));
+        if (bb) atomicOr(&c.st->flags, 4);
     }
 }
 
