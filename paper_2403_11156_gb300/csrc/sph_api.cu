@@ -879,8 +879,10 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
             const sph_rigid_desc &rd = d.bodies[k];
             BodyDev &B = hb[q.body_off + k];
             B.mass = rd.mass;
+            B.inv_mass = 1.0 / rd.mass;
             for (int a = 0; a < 3; ++a) {
                 B.inertia[a] = rd.inertia[a];
+                B.inv_inertia[a] = 1.0 / rd.inertia[a];
                 B.com[a] = rd.com[a];
                 B.vel[a] = rd.vel[a];
                 B.omega[a] = rd.omega[a];

@@ -763,7 +763,11 @@ __global__ void k_step_end(Ptrs P)
         const SceneDev &sc = P.scenes[B.scene];
         const double dt = (double)P.st[B.scene].dt;
         const double fs = sc.strong ? 0.0 : 1.0;   // strong coupling applied the fluid's impulses already
-        for (int a = 0; a < 3; ++a) B.vel[a] += dt * (fs * B.force[a] / B.mass + (double)sc.g[a]);
+        // FP64 division is a long dependent sequence on this GPU: the body record carries
+        // 1/m and 1/I, and the quaternion is renormalised with one reciprocal square root
+        const double inv_m = B.inv_mass;
+        const double inv_i[3] = {B.inv_inertia[0], B.inv_inertia[1], B.inv_inertia[2]};
+        for (int a = 0; a < 3; ++a) B.vel[a] += dt * (fs * B.force[a] * inv_m + (double)sc.g[a]);
         for (int a = 0; a < 3; ++a) B.com[a] += dt * B.vel[a];
         double w = B.quat[0], x = B.quat[1], y = B.quat[2], z = B.quat[3];
         double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
@@ -776,7 +780,7 @@ __global__ void k_step_end(Ptrs P)
                 Ii[a][e] = 0.0;
                 for (int q = 0; q < 3; ++q) {
                     Iw[a][e] += R[a][q] * B.inertia[q] * R[e][q];
-                    Ii[a][e] += R[a][q] / B.inertia[q] * R[e][q];
+                    Ii[a][e] += R[a][q] * inv_i[q] * R[e][q];
                 }
             }
         double o[3] = {B.omega[0], B.omega[1], B.omega[2]};
@@ -792,8 +796,8 @@ __global__ void k_step_end(Ptrs P)
         double dy = 0.5 * (oy * w + oz * x - ox * z);
         double dz = 0.5 * (oz * w + ox * y - oy * x);
         w += dt * dw; x += dt * dx; y += dt * dy; z += dt * dz;
-        double nq = sqrt(w * w + x * x + y * y + z * z);
-        B.quat[0] = w / nq; B.quat[1] = x / nq; B.quat[2] = y / nq; B.quat[3] = z / nq;
+        const double inv_nq = rsqrt(w * w + x * x + y * y + z * z);
+        B.quat[0] = w * inv_nq; B.quat[1] = x * inv_nq; B.quat[2] = y * inv_nq; B.quat[3] = z * inv_nq;
         // no contact model (the paper delegates contact to PyBullet): the bounding sphere
         // is clamped inside the domain, and each clamp is counted
         for (int a = 0; a < 3; ++a) {

@@ -83,6 +83,7 @@ struct SceneState {
 // Rigid body state (device, FP64).
 struct BodyDev {
     double mass, inertia[3];
+    double inv_mass, inv_inertia[3];  // reciprocals, set with the mass (FP64 division is slow)
     double com[3], quat[4], vel[3], omega[3];
     double force[3], torque[3];
     double radius;                    // bounding sphere of its boundary particles

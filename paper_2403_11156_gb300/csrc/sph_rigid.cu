@@ -259,16 +259,19 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int phase)
     const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
                             {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
                             {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+    // the body record's reciprocals (FP64 division is a long dependent sequence here)
+    const double inv_m = B.inv_mass;
+    const double inv_i[3] = {B.inv_inertia[0], B.inv_inertia[1], B.inv_inertia[2]};
     for (int a = 0; a < 3; ++a) {
         B.force[a] += s_f[a];
         B.torque[a] += s_f[3 + a];
-        B.vel[a] += dt * s_f[a] / B.mass;
+        B.vel[a] += dt * s_f[a] * inv_m;
     }
     for (int a = 0; a < 3; ++a) {
         double d = 0.0;
         for (int e = 0; e < 3; ++e) {
             double ii = 0.0;
-            for (int q = 0; q < 3; ++q) ii += R[a][q] / B.inertia[q] * R[e][q];
+            for (int q = 0; q < 3; ++q) ii += R[a][q] * inv_i[q] * R[e][q];
             d += ii * s_f[3 + e];
         }
         B.omega[a] += dt * d;
