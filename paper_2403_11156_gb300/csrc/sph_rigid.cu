@@ -75,20 +75,6 @@ __global__ void __launch_bounds__(kBlock) k_boundary_psi(Ptrs P)
     reinterpret_cast<float *>(P.bpos_s + b)[3] = sc.rho0 / (sc.sigma * (1.0f + ws));
 }
 
-__device__ double block_sum_d(double v, double *sh)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < kBlock / 32; ++k) t += sh[k];
-    return t;
-}
-
 // Force and torque of the fluid on each body of the scene (the T lanes of a particle share
 // its boundary list; the block sums add all lanes), as per-block partials.  INC = false:
 // weakly coupled scenes, from the step's total applied stiffness after the solves;
@@ -97,7 +83,7 @@ __device__ double block_sum_d(double v, double *sh)
 template <int T, bool INC>
 __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int phase)
 {
-    __shared__ double sh[kBlock / 32];
+    __shared__ double sh6[kBlock / 32][6];
     kernel_enter(P.ctl, INC ? KID_BFORCE_INC : KID_BFORCE);
     const Lane<T> c = lane_ctx<T>(P);
     const SceneDev &sc = *c.sc;
@@ -159,9 +145,26 @@ __global__ void __launch_bounds__(kBlock) k_body_force(Ptrs P, int phase)
             }
         }
         if (INC && !any) continue;   // the apply kernel skips this block for body k
-        for (int a = 0; a < 6; ++a) {
-            double t = any ? block_sum_d(f[a], sh) : 0.0;
-            if (threadIdx.x == 0) P.body_partial[((int64_t)(sc.body_off + k) * 6 + a) * P.ntblk + blockIdx.x] = t;
+        double *part = P.body_partial + (int64_t)(sc.body_off + k) * 6 * P.ntblk + blockIdx.x;
+        if (!any) {
+            if (threadIdx.x < 6) part[(int64_t)threadIdx.x * P.ntblk] = 0.0;
+            continue;
+        }
+        // the six components in one pass (each the same butterfly and the same fold over the
+        // warps, in the same order, as a sum of its own): two barriers instead of twelve
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) f[a] += __shfl_xor_sync(0xffffffffu, f[a], o);
+        __syncthreads();   // the previous body's reads of sh6 are done
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int a = 0; a < 6; ++a) sh6[threadIdx.x >> 5][a] = f[a];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) t += sh6[w][threadIdx.x];
+            part[(int64_t)threadIdx.x * P.ntblk] = t;
         }
     }
 }
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256) k_body_reduce(Ptrs P)
 // v += dt F / M, omega += dt I^-1 tau (world inertia of the step's orientation).
 __global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int phase)
 {
-    __shared__ double sh[8];
+    __shared__ double sh6[8][6];
     __shared__ double s_f[6];
     kernel_enter(P.ctl, KID_BAPPLY);
     const int body = blockIdx.x;
@@ -239,18 +242,20 @@ __global__ void __launch_bounds__(256) k_body_apply(Ptrs P, int phase)
         if (!((P.blk_touch[sc.tblk_first + q] >> k) & 1ull)) continue;
         for (int a = 0; a < 6; ++a) f[a] += P.body_partial[((int64_t)body * 6 + a) * P.ntblk + sc.tblk_first + q];
     }
-    for (int a = 0; a < 6; ++a) {
-        double t = f[a];
+    // the six components in one pass (each the same butterfly and fold over the warps as a
+    // sum of its own)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < 8; ++w) tot += sh[w];
-            s_f[a] = tot;
-        }
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f[a] += __shfl_xor_sync(0xffffffffu, f[a], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) sh6[threadIdx.x >> 5][a] = f[a];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += sh6[w][threadIdx.x];
+        s_f[threadIdx.x] = tot;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
