@@ -669,6 +669,7 @@ sph_status create_impl(const sph_scene_desc *descs, int32_t n, const sph_allocat
         q.inv_h = (float)(1.0 / h);
         q.m = (float)((double)d.rest_density * 8.0 * r * r * r);
         q.rho0 = d.rest_density;
+        q.err_scale = d.n_fluid > 0 ? 1.0 / ((double)d.n_fluid * (double)d.rest_density) : 0.0;
         q.sigma = (float)(8.0 / (kPi * h * h * h));
         q.kgrad = (float)(48.0 / (kPi * h * h * h * h));
         double gs = (double)q.m * 48.0 / (kPi * h * h * h * h);

@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kCheckThreads) k_solver_check(Ptrs P, cudaGrap
         for (int k = lane; k < nfold; k += 32) t += __ldcg(P.partial2 + qd.tblk_first + k);
         t = warp_sum(t);
         if (lane == 0) {
-            double err = qd.nf > 0 ? t / (double)qd.nf / (double)qd.rho0 : 0.0;
+            double err = t * qd.err_scale;   // FP64 division is a long sequence here
             if (S == 0) err *= (double)qs.dt;
             if (qs.it[S] == 0) qs.err0[S] = err;
             qs.err[S] = err;

@@ -58,6 +58,7 @@ struct SceneDev {
     int32_t strong;                   // strong rigid coupling: bodies pushed during the solves
     float learned_frac;               // fraction of the network's stiffness warm-starting it
     int32_t learned_gate;             // the network runs only above this many density iterations
+    double err_scale;                 // 1 / (nf rho0): a solve's error sum to its mean per rho0
 };
 
 // Per-scene mutable state (device).
