@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P
         const int32_t cz = cell_coord(pi.z, sc.origin[2], sc.cell, sc.dims[2]);
         const int32_t R = sc.R;
         const float h2 = sc.h2, cull2 = sc.cull2, cs = sc.cell;
+        const unsigned long long pixy = pack_xy(pi.x, pi.y);   // for the packed candidate test
         // offset of the particle inside its cell, per axis: the distance from the particle
         // to a stencil cell d cells away is at least gap(d) (zero for d = 0)
         const float ox = pi.x - fmaf((float)cx, cs, sc.origin[0]);
@@ -190,8 +191,7 @@ __global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P
                         auto bits = [&](uint32_t b0, uint32_t b1) {
                             uint32_t mk = 0u;
                             for_range<4, 1>(P.pos_s, b0, b1, [&](uint32_t j, float4 pj) {
-                                float dx, dy2, dz2;
-                                mk |= (uint32_t)(pred_d2(pi, pj, dx, dy2, dz2) < h2) << (j - b0);
+                                mk |= (uint32_t)(pred_d2_xy2(pixy, pi.z, pj) < h2) << (j - b0);
                             });
                             return mk;
                         };
