@@ -482,6 +482,8 @@ def run_reference(args, rank, world):
         return
     import oracle
     oracle.build()
+    # the host's cores, however the process was launched (torchrun sets OMP_NUM_THREADS=1)
+    oracle.set_num_threads(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     d = reference_sample()
     o = oracle.Scene(d)
     for _ in range(args.warmup):
