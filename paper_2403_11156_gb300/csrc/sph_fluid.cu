@@ -189,10 +189,20 @@ __global__ void __launch_bounds__(kBlock, T == 1 ? 9 : 8) k_density_alpha(Ptrs P
                         // mask (no store or counter per candidate, most are rejected), and
                         // the hits are appended in candidate order from the mask
                         auto bits = [&](uint32_t b0, uint32_t b1) {
+                            // four candidates per batch: their loads issue together, and their
+                            // hits are combined at fixed shifts before one shift into place
                             uint32_t mk = 0u;
-                            for_range<4, 1>(P.pos_s, b0, b1, [&](uint32_t j, float4 pj) {
-                                mk |= (uint32_t)(pred_d2_xy2(pixy, pi.z, pj) < h2) << (j - b0);
-                            });
+                            uint32_t j = b0;
+                            for (; j + 3u < b1; j += 4u) {
+                                float4 pc[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) pc[u] = __ldg(P.pos_s + j + u);
+                                uint32_t q = 0u;
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) q |= (uint32_t)(pred_d2_xy2(pixy, pi.z, pc[u]) < h2) << u;
+                                mk |= q << (j - b0);
+                            }
+                            for (; j < b1; ++j) mk |= (uint32_t)(pred_d2_xy2(pixy, pi.z, __ldg(P.pos_s + j)) < h2) << (j - b0);
                             return mk;
                         };
                         uint64_t m = bits(jb, min(je, jb + 32u));
