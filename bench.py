@@ -54,14 +54,14 @@ BOUNDARY_BYTES = 16                             # x_b, Psi_b per boundary partic
 # now (the roofline's `traffic`; null for any other kernel or configuration).  Filled from
 # the committed captures (profiles/*_dam_break_1.2M.md); a kernel changed since its capture
 # has no entry.
-TRAFFIC = {("density_alpha", 1, 4, 27): 82.21e6 + 167.26e6,
+TRAFFIC = {("density_alpha", 1, 4, 27): 82.70e6 + 169.47e6,
            ("dens_pass_a", 1, 4, 27): 211.59e6 + 4.72e6,
            ("dens_pass_b", 1, 4, 27): 199.69e6 + 4.33e6}
 # L1 data-pipe (LSU) wavefronts per launch measured by ncu in the same captures
 # (l1tex__data_pipe_lsu_wavefronts, per-SM average x 152 SMs).  The pipe takes one wavefront per
 # SM per cycle, so over the live launch time this is the fraction of the roof that binds the
 # neighbour gathers.
-L1_WAVEFRONTS = {("density_alpha", 1, 4, 27): 616405.65 * 152,
+L1_WAVEFRONTS = {("density_alpha", 1, 4, 27): 617053.83 * 152,
                  ("dens_pass_a", 1, 4, 27): 203077.14 * 152,
                  ("dens_pass_b", 1, 4, 27): 124865.32 * 152}
 # FP32 operations per neighbour pair in the list sweeps (distance, spline gradient, dot)
